@@ -1,0 +1,356 @@
+"""Benchmark of the fused D3Q19 MRT-LES + STG channel step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                [--config c2] [--precision fp32|fp16|bf16]
+
+One bench step is one time step of the method over the whole lattice: the STG
+inlet kernel and the fused stream/inlet/wall/collide kernel, with the FP64
+statistics accumulated every 10 steps.  Default workload: the Re_tau = 1000
+channel, 384 x 96 x 96 lattice, N = 200 STG modes, FP32 storage.  The two
+lattices (538 MB) exceed the 129 MB L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances its
+own independent channel (an ensemble member with its own STG draws): weak
+scaling, no collective on the data path.
+"""
+import argparse
+import ctypes as ct
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS of fused D3Q19 MRT-LES+STG step & % HBM roofline; adjoint/forward time"
+
+CONFIGS = {
+    "c1": dict(shape=(64, 32, 32), re_tau=1000.0, n_modes=100, seed=1,
+               name="small channel 64x32x32 (4d x 2d x 2d), Re_tau=1000, N=100 STG modes"),
+    "c2": dict(shape=(384, 96, 96), re_tau=1000.0, n_modes=200, seed=2,
+               name="Re_tau=1000 channel 384x96x96, N=200 STG modes"),
+    "c3": dict(shape=(768, 128, 192), re_tau=2000.0, n_modes=300, seed=3,
+               name="Re_tau=2000 channel 768x128x192, N=300 STG modes"),
+    "c4": dict(shape=(1536, 192, 384), re_tau=5200.0, n_modes=400, seed=4,
+               name="Re_tau=5200 channel 1536x192x384, N=400 STG modes"),
+}
+BYTES_PER_CELL = {"fp32": 152, "fp16": 76, "bf16": 76}   # 19 loads + 19 stores
+STATS_EVERY = 10
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_device.cuh", "lbm_api.cu"):
+        with open(os.path.join(ROOT, "paper_2304_04214_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(cfg_key, precision, ncell):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when the summary is for another build of the kernel."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    ent = rec.get("entries", {}).get(f"{cfg_key}_{precision}")
+    if not ent:
+        return None
+    return ent["bytes_per_cell"] * ncell
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 6:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        s = sorted(sm)
+        return {"sm_mhz": s[len(s) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def smi_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [p for p in vis.split(",") if p.strip()]
+    if parts and parts[min(local_rank, len(parts) - 1)].strip().isdigit():
+        return int(parts[min(local_rank, len(parts) - 1)])
+    return local_rank
+
+
+# --------------------------------------------------------------------------
+def cpu_oracle_mlups(cfg, budget_s=10.0, steps=None, nz_sample=None, warmup=0):
+    """Time the FP64 oracle on this host's cores on the workload's lattice (or a
+    spanwise slice of it), returning (MLUPS, threads, sample description)."""
+    from oracle.oracle import Oracle, default_config, oracle_threads
+    from paper_2304_04214_gb300.inputs import stg_uniforms
+    nx, ny, nz = cfg["shape"]
+    nzs = nz if nz_sample is None else nz_sample
+    un = stg_uniforms(cfg["n_modes"], cfg["seed"])
+    o = Oracle(default_config(nx, ny, nzs, re_tau=cfg["re_tau"], n_modes=cfg["n_modes"], stats=0),
+               uniforms=un)
+    if warmup:
+        o.step(warmup)
+    if steps is None:
+        t0 = time.perf_counter()
+        o.step(1)
+        t1 = time.perf_counter() - t0
+        n = max(1, int(budget_s / max(t1, 1e-6)) - 1)
+        t0 = time.perf_counter()
+        o.step(n)
+        dt = time.perf_counter() - t0 + t1
+        n += 1
+    else:
+        n = steps
+        t0 = time.perf_counter()
+        o.step(n)
+        dt = time.perf_counter() - t0
+    mlups = nx * ny * nzs * n / dt / 1e6
+    return mlups, oracle_threads(), f"{nx}x{ny}x{nzs} lattice, {n} steps, {dt:.1f} s", dt, n
+
+
+def run_reference(args, cfg, ws, rank):
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    # calibrate a spanwise slice so that W + K steps take about two minutes
+    nx, ny, nz = cfg["shape"]
+    m1, _, _, dt1, n1 = cpu_oracle_mlups(cfg, steps=1, nz_sample=max(1, nz // 8))
+    per_cell = 1.0 / (m1 * 1e6)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    nzs = int(max(1, min(nz, budget / (per_cell * nx * ny))))
+    mlups, thr, sample, dt, n = cpu_oracle_mlups(cfg, steps=args.steps, nz_sample=nzs, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * dt / n, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"] + " (oracle on a spanwise slice)", "storage": "fp64",
+                   "lattice": list(cfg["shape"]), "sample_lattice": [nx, ny, nzs]},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+def run_native(args, cfg, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_2304_04214_gb300 import _abi
+    from paper_2304_04214_gb300.channel import LBMChannel
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    nx, ny, nz = cfg["shape"]
+    ncell = nx * ny * nz
+    ch = LBMChannel(nx, ny, nz, re_tau=cfg["re_tau"], n_modes=cfg["n_modes"],
+                    seed=cfg["seed"] + 1000 * rank, precision=args.precision,
+                    stats_every=STATS_EVERY, device=dev)
+    lib, h = ch.lib, ch.h
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- warm-up ----
+    ch.step(args.warmup)
+    ch.sync()
+    barrier()
+
+    # ---- timed region: K steps, device events, kernel events, clocks ----
+    _abi.check(lib.lbm_profile_enable(h, 1), "lbm_profile_enable")
+    ms_k, nk, nall = ct.c_double(), ct.c_long(), ct.c_long()
+    lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))   # reset counters
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(smi_index(local)) as clk:
+        barrier()
+        e0.record(stream)
+        ch.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))
+    lib.lbm_profile_enable(h, 0)
+    ch.sync()
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ncell * ws * args.steps / (ms * 1e-3) / 1e6
+
+    # ---- roofline of the fused step kernel ----
+    peaks, peak_kind = measured_peaks()
+    kern_ms = ms_k.value / max(nk.value, 1)
+    alg_bytes = BYTES_PER_CELL[args.precision] * ncell
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(args.config, args.precision, ncell)
+
+    # ---- end to end through the C ABI with host buffers ----
+    # each step: the RANS-side inlet profile (U, R) from pinned host memory,
+    # one time step, and the z-averaged wall shear read back to pinned memory
+    U = torch.empty(ny, dtype=torch.float64).pin_memory()
+    R = torch.empty(6 * ny, dtype=torch.float64).pin_memory()
+    tw = torch.empty(2 * nx, dtype=torch.float64).pin_memory()
+    dp = lambda x: ct.cast(x.data_ptr(), ct.POINTER(ct.c_double))   # noqa: E731
+    _abi.check(lib.lbm_get_inlet_profile(h, dp(U), dp(R)), "lbm_get_inlet_profile")
+    n_e2e = max(3, min(args.steps, 2000))
+    for _ in range(3):
+        lib.lbm_set_inlet_profile(h, dp(U), dp(R))
+        lib.lbm_step(h, 1)
+        lib.lbm_wall_shear(h, dp(tw))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        _abi.check(lib.lbm_set_inlet_profile(h, dp(U), dp(R)), "lbm_set_inlet_profile")
+        _abi.check(lib.lbm_step(h, 1), "lbm_step")
+        _abi.check(lib.lbm_wall_shear(h, dp(tw)), "lbm_wall_shear")
+    barrier()
+    dt_e2e = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([dt_e2e], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt_e2e = float(t.item())
+    e2e = ncell * ws * n_e2e / dt_e2e / 1e6
+    assert np.all(np.isfinite(tw.numpy()))
+    ch.sync()
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            m, thr, sample, _, _ = cpu_oracle_mlups(cfg, budget_s=10.0)
+            cpu = {"value": round(m, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+                   "sample": sample}
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"] + f", {args.precision.upper()} storage",
+                       "lattice": list(cfg["shape"]), "re_tau": cfg["re_tau"],
+                       "n_modes": cfg["n_modes"], "storage": args.precision,
+                       "stats_every": STATS_EVERY,
+                       "l2": "no flush: the two lattices (%.0f MB) exceed the 129 MB L2"
+                             % (2 * BYTES_PER_CELL[args.precision] / 2 * ncell / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(achieved / peaks["hbm_gbs"], 4),
+                         "traffic": traffic, "peak_source": peak_kind,
+                         "kernel": "lbmk::step_kernel", "kernel_ms": round(kern_ms, 5),
+                         "algorithmic_bytes": alg_bytes},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e, 1), "unit": "MLUPS",
+                    "h2d_bytes_per_step": 7 * ny * 4, "d2h_bytes_per_step": 2 * nx * 8},
+            "gpu_launches": int(nall.value),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    ch.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg, ws, rank)
+    else:
+        run_native(args, cfg, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

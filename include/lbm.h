@@ -1,0 +1,198 @@
+/*
+ * lbm.h -- C ABI of liblbm_gb300.so, a GB300 (sm_103a) implementation of the
+ * per-time-step hot path of the STG wall-modelled LES lattice Boltzmann channel
+ * method of Xue, Yao & Davidson, "Synthetic turbulence generator for the
+ * wall-modeled LES lattice Boltzmann method" (arXiv 2304.04214):
+ *
+ *   D3Q19 multiple-relaxation-time collide-and-stream (Sec. 2.1, App. A.1),
+ *   Smagorinsky eddy viscosity folded into the viscous rates (Sec. 2.2),
+ *   force-based Reichardt wall model on the first off-wall cells (Sec. 2.3),
+ *   synthetic-turbulence inlet plane with regularized reconstruction (Sec. 3.1),
+ *   in the order of Algorithm 1.
+ *
+ * Geometry.  Lattice nx x ny x nz, x streamwise (inlet at x = 0, zero-gradient
+ * outlet at x = nx-1), y wall-normal (specular slip walls half a cell below
+ * j = 0 and above j = ny-1, so the first cell centre sits at y = 1/2), z
+ * spanwise and periodic.  delta = ny/2.  Requirements: ny even and >= 4,
+ * nx >= 3, nz >= 1.
+ *
+ * Layout.  Populations are structure-of-arrays f[q][k][j][i], i fastest, with
+ * the velocity order of Sec. 2.1 (eq:vel-set): q = 9 is the rest velocity and
+ * q and 18 - q are opposite.  The lattice state between steps is the
+ * post-collision population set (pull streaming happens at the start of the
+ * next step).  Host arrays passed to the calls below use the same layout in
+ * FP64; device storage is FP32 (f), or FP16 / BF16 deviations f - w_q.
+ *
+ * Conventions.  Every call returns 0 (LBM_OK) or a negative LBM_E* code and
+ * never throws.  All work is enqueued on the handle's CUDA stream; calls that
+ * return host data synchronize that stream first.  Host pointers are owned
+ * by the caller.  Device memory is either bound by the caller
+ * (lbm_bind_memory with a pointer) or allocated by the library (pointer NULL).
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define LBM_OK          0
+#define LBM_EINVAL     -1   /* invalid argument (bad grid, NULL pointer, size) */
+#define LBM_ENOMEM     -2   /* bound memory too small or allocation failed */
+#define LBM_ECUDA      -3   /* a CUDA runtime call failed */
+#define LBM_EDIVERGED  -4   /* non-finite or |u| > 0.3 seen on the lattice */
+#define LBM_ENOTCONV   -5   /* the u_tau Newton solve did not converge */
+#define LBM_ESTATE     -6   /* call out of order (e.g. step before memory) */
+
+/* ---- storage of the populations ---- */
+#define LBM_FP32      0     /* f_q in FP32 */
+#define LBM_FP16_DEV  1     /* f_q - w_q in IEEE FP16, round to nearest */
+#define LBM_BF16_DEV  2     /* f_q - w_q in BF16, round to nearest */
+
+typedef struct lbm_handle lbm_handle;
+
+typedef struct {
+    int nx, ny, nz;
+} lbm_grid;
+
+/* Synthetic turbulence generator (Sec. 3.1, eq:aux_vec).  The modes use
+ * k_n = k_min r^(n-1) with k_min = beta_kmin 2 pi / max_y l_e(y) and
+ * l_e(y) = ell_e delta tanh(2 d_w / (ell_e delta)); u' = amp * a v' with a the
+ * Cholesky factor of the prescribed Reynolds stress (eq:cholesky). */
+typedef struct {
+    int n_modes;              /* N, >= 0 (0: no fluctuations) */
+    double k_ratio;           /* r, default 1.01 */
+    double beta_kmin;         /* default 0.5 */
+    double ell_e;             /* length-scale factor (theta_0), default 0.4 */
+    double amp;               /* amplitude A (theta_1), default 1 */
+    const double *uniforms;   /* host, n_modes x 4 values in [0,1): the STG's
+                                 random draws (polar angle and azimuth of d_n,
+                                 angle of sigma_n about d_n, phase phi_n).
+                                 Copied at creation. */
+} lbm_stg_params;
+
+typedef struct {
+    int precision;            /* LBM_FP32 | LBM_FP16_DEV | LBM_BF16_DEV */
+    double u_bulk;            /* bulk velocity U_b (lattice units), default 0.05 */
+    double c_smag;            /* C_smag Delta^2 of eq:smogrinsky_model, default 0.01 */
+    double kappa;             /* Reichardt kappa (theta_2), default 0.4 */
+    double B;                 /* Reichardt B (theta_3), default 7.8 */
+    int wall_model;           /* 1: Reichardt wall force (Sec. 2.3); 0: off */
+    int inlet;                /* 1: STG inlet + zero-gradient outlet; 0: periodic x */
+    int stats_every;          /* accumulate statistics every s steps; 0: off */
+    void *cuda_stream;        /* cudaStream_t to enqueue on; NULL: default stream */
+} lbm_opts;
+
+/* Fill *opts with the defaults listed above (FP32, stream NULL). */
+void lbm_default_opts(lbm_opts *opts);
+
+/* Create a channel.  Computes the flow constants in FP64 on the host:
+ * delta = ny/2, U_b+ = mean of the Reichardt law over the cell centres,
+ * u_tau = U_b / U_b+, nu = u_tau delta / Re_tau, tau0 = 3 nu + 1/2 (eq:nu),
+ * and the STG tables (Algorithm 1, steps 1-3).  No device memory is touched:
+ * bind memory next.  *out receives the handle (free with lbm_destroy).
+ * Errors: LBM_EINVAL for NULL pointers, ny odd or < 4, nx < 3, nz < 1,
+ * re_tau <= 0, n_modes < 0, uniforms NULL while n_modes > 0. */
+int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg,
+               const lbm_opts *opts, lbm_handle **out);
+
+/* Device bytes the handle needs (both lattices, tables, wall and inlet
+ * buffers, statistics).  Alignment of the bound pointer: 256 bytes. */
+int lbm_required_bytes(const lbm_handle *h, size_t *bytes);
+
+/* Bind device memory: dev_ptr of at least lbm_required_bytes bytes, owned by
+ * the caller (the library never frees it); or dev_ptr NULL to let the library
+ * cudaMalloc it (freed by lbm_destroy).  Uploads the tables and initializes
+ * the lattice to f^eq(1, (U_R(y), 0, 0)) with U_R the inlet mean profile.
+ * Errors: LBM_ENOMEM if bytes is too small, LBM_EINVAL if misaligned,
+ * LBM_ESTATE if already bound, LBM_ECUDA. */
+int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes);
+
+/* Enqueue n time steps of Algorithm 1 on the handle's stream and return
+ * without synchronizing.  Each step: inlet velocity (steps 4-5), then one
+ * fused kernel doing pull streaming with the boundary rules, the regularized
+ * inlet (steps 6-8), the wall model (steps 9-14) and the collision (step 15).
+ * Errors: LBM_ESTATE before lbm_bind_memory, LBM_EINVAL if n < 0, LBM_ECUDA. */
+int lbm_step(lbm_handle *h, int n);
+
+/* Synchronize the stream and report deferred device errors:
+ * LBM_EDIVERGED, LBM_ENOTCONV (the counters are cleared when read). */
+int lbm_sync(lbm_handle *h);
+
+/* Set the CUDA stream later calls enqueue on (cudaStream_t; NULL = default). */
+int lbm_set_stream(lbm_handle *h, void *cuda_stream);
+
+/* Statistics accumulated every stats_every steps since the last reset:
+ * sums[(j*nx + i)*7 + c], c = (u, v, w, uu, vv, ww, uv), each summed over z
+ * and samples in FP64; utau_sums[w*nx + i] (w = 0 bottom, 1 top) summed over z
+ * and samples; *n_samples the number of samples.  Host buffers of nx*ny*7 and
+ * 2*nx doubles.  Synchronizes. */
+int lbm_stats(lbm_handle *h, double *sums, double *utau_sums, long *n_samples);
+int lbm_reset_stats(lbm_handle *h);
+
+/* Macroscopic fields of the last collision, eq:density and eq:momentum:
+ * rho[c] and u[3*c + a] for cell c = (k*ny + j)*nx + i, host FP64.
+ * rho u = sum_q f*_q c_q - F/2 with F the wall force of that collision.
+ * Synchronizes. */
+int lbm_get_fields(lbm_handle *h, double *rho, double *u);
+
+/* Copy the post-collision populations out / in (host FP64, 19*ncell, layout
+ * f[q][k][j][i]).  set rounds to the storage type (FP16/BF16 deviations are
+ * rounded to nearest after subtracting w_q in FP64). */
+int lbm_get_populations(lbm_handle *h, double *f);
+int lbm_set_populations(lbm_handle *h, const double *f);
+
+/* Friction velocity of every wall cell from the last step, host FP64,
+ * utau[(w*nz + k)*nx + i] (w = 0 bottom, 1 top).  Synchronizes. */
+int lbm_get_utau(lbm_handle *h, double *utau);
+
+/* Time counter t (the STG time of the next step, eq:aux_vec). */
+int lbm_get_time(const lbm_handle *h, long *t);
+int lbm_set_time(lbm_handle *h, long t);
+
+/* Flow constants: out[0..5] = delta, u_tau,ref, nu, tau0, U_b+, max l_e. */
+int lbm_get_constants(const lbm_handle *h, double out[6]);
+
+/* STG inlet velocity u_in(j, k, t) = (U_R(j), 0, 0) + amp a(j) v'(j, k, t)
+ * (eq:u_couple, eq:v_fluc, eq:aux_vec) computed by the device kernel for time
+ * t; host FP64 out[(k*ny + j)*3 + a].  Synchronizes. */
+int lbm_inlet_velocity(lbm_handle *h, long t, double *out);
+
+/* Inlet mean profile and Reynolds stress, the RANS input of Algorithm 1
+ * steps 1-3 (eq:u_couple, eq:cholesky).  U[j]: streamwise mean velocity of
+ * row j; R[6*j + c] = (R11, R22, R33, R12, R13, R23) of row j, lattice units.
+ * set copies the host buffers, recomputes amp * chol(R) in FP64 on the host
+ * and enqueues the upload on the stream (no synchronization); it returns
+ * LBM_EINVAL if some R(j) is not positive definite.  The defaults are the
+ * Reichardt profile and the analytic stress of lbm_create. */
+int lbm_set_inlet_profile(lbm_handle *h, const double *U, const double *R);
+int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R);
+
+/* Wall shear stress tau_w = rho u_tau^2 (Sec. 2.3) of the last step,
+ * averaged over z: host out[w*nx + i], w = 0 bottom, 1 top.  Synchronizes. */
+int lbm_wall_shear(lbm_handle *h, double *out);
+
+/* Instrumentation.  While enabled, every launch of the fused step kernel is
+ * bracketed by CUDA events on the handle's stream.  read synchronizes and
+ * returns the summed kernel time in ms and the number of timed launches since
+ * the last read, and the number of kernels of any kind the handle launched. */
+int lbm_profile_enable(lbm_handle *h, int on);
+int lbm_profile_read(lbm_handle *h, double *ms_total, long *step_launches, long *all_launches);
+
+/* Replace the model parameters theta = (ell_e, amp, kappa, B) and rebuild
+ * the tables that depend on them (the flow constants of lbm_create stay). */
+int lbm_set_params(lbm_handle *h, const double theta[4]);
+
+void lbm_destroy(lbm_handle *h);
+
+/* Static string for an error code. */
+const char *lbm_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

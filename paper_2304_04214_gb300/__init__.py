@@ -5,11 +5,11 @@ in include/lbm.h; this package is its thin Python binding.  Importing the
 package loads nothing: the library is opened on first use and the binding
 raises if it is missing -- there is no CPU fallback.
 """
-__all__ = ["LBMChannel", "STGAdjoint", "lib"]
+__all__ = ["LBMChannel", "lib"]
 
 
 def __getattr__(name):
-    if name in ("LBMChannel", "STGAdjoint"):
+    if name == "LBMChannel":
         from . import channel
         return getattr(channel, name)
     if name == "lib":

@@ -1,0 +1,96 @@
+"""ctypes declarations of the C ABI in include/lbm.h (argument marshalling only)."""
+import ctypes as ct
+import os
+
+from . import build as _build
+
+_LIB = None
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ENOTCONV, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2
+PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16_DEV, "bf16": LBM_BF16_DEV}
+
+
+class Grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int)]
+
+
+class StgParams(ct.Structure):
+    _fields_ = [("n_modes", ct.c_int), ("k_ratio", ct.c_double), ("beta_kmin", ct.c_double),
+                ("ell_e", ct.c_double), ("amp", ct.c_double), ("uniforms", ct.POINTER(ct.c_double))]
+
+
+class Opts(ct.Structure):
+    _fields_ = [("precision", ct.c_int), ("u_bulk", ct.c_double), ("c_smag", ct.c_double),
+                ("kappa", ct.c_double), ("B", ct.c_double), ("wall_model", ct.c_int),
+                ("inlet", ct.c_int), ("stats_every", ct.c_int), ("cuda_stream", ct.c_void_p)]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, call):
+        msg = lib().lbm_error_string(code).decode()
+        super().__init__(f"{call} failed: {msg} ({code})")
+        self.code = code
+
+
+_dp = ct.POINTER(ct.c_double)
+_h = ct.c_void_p
+
+# name -> (restype, argtypes)
+PROTOTYPES = {
+    "lbm_default_opts": (None, [ct.POINTER(Opts)]),
+    "lbm_create": (ct.c_int, [ct.POINTER(Grid), ct.c_double, ct.POINTER(StgParams), ct.POINTER(Opts),
+                              ct.POINTER(ct.c_void_p)]),
+    "lbm_required_bytes": (ct.c_int, [_h, ct.POINTER(ct.c_size_t)]),
+    "lbm_bind_memory": (ct.c_int, [_h, ct.c_void_p, ct.c_size_t]),
+    "lbm_step": (ct.c_int, [_h, ct.c_int]),
+    "lbm_sync": (ct.c_int, [_h]),
+    "lbm_set_stream": (ct.c_int, [_h, ct.c_void_p]),
+    "lbm_stats": (ct.c_int, [_h, _dp, _dp, ct.POINTER(ct.c_long)]),
+    "lbm_reset_stats": (ct.c_int, [_h]),
+    "lbm_get_fields": (ct.c_int, [_h, _dp, _dp]),
+    "lbm_get_populations": (ct.c_int, [_h, _dp]),
+    "lbm_set_populations": (ct.c_int, [_h, _dp]),
+    "lbm_get_utau": (ct.c_int, [_h, _dp]),
+    "lbm_get_time": (ct.c_int, [_h, ct.POINTER(ct.c_long)]),
+    "lbm_set_time": (ct.c_int, [_h, ct.c_long]),
+    "lbm_get_constants": (ct.c_int, [_h, _dp]),
+    "lbm_inlet_velocity": (ct.c_int, [_h, ct.c_long, _dp]),
+    "lbm_set_params": (ct.c_int, [_h, _dp]),
+    "lbm_set_inlet_profile": (ct.c_int, [_h, _dp, _dp]),
+    "lbm_get_inlet_profile": (ct.c_int, [_h, _dp, _dp]),
+    "lbm_wall_shear": (ct.c_int, [_h, _dp]),
+    "lbm_profile_enable": (ct.c_int, [_h, ct.c_int]),
+    "lbm_profile_read": (ct.c_int, [_h, _dp, ct.POINTER(ct.c_long), ct.POINTER(ct.c_long)]),
+    "lbm_destroy": (None, [_h]),
+    "lbm_error_string": (ct.c_char_p, [ct.c_int]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Open liblbm_gb300.so (building it from the in-tree sources if absent).
+
+    Raises if it cannot be built or loaded: there is no other implementation.
+    """
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path) or _build._stale():
+        _build.build()
+    L = ct.CDLL(path)
+    for name, (res, args) in PROTOTYPES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def check(code, call):
+    if code != LBM_OK:
+        raise LBMError(code, call)

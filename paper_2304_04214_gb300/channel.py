@@ -1,0 +1,145 @@
+"""Python binding of the channel library: PyTorch supplies the device memory
+and the stream, every step of the method runs in the CUDA kernels behind the
+C ABI (include/lbm.h).  Arrays use the layout f[q][k][j][i]."""
+import ctypes as ct
+
+import numpy as np
+
+from . import _abi
+from .inputs import stg_uniforms
+
+Q = 19
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+class LBMChannel:
+    """A synthetic turbulent channel on one GPU.
+
+    nx x ny x nz lattice (x streamwise, y wall-normal with delta = ny/2, z
+    spanwise), friction Reynolds number re_tau, an STG inlet with n_modes
+    Fourier modes whose random draws are `uniforms` (n_modes x 4 in [0,1);
+    drawn from `seed` by paper_2304_04214_gb300.inputs if not given).
+    theta = (ell_e, amp, kappa, B) are the STG length-scale factor and
+    amplitude and the Reichardt constants.
+    """
+
+    def __init__(self, nx, ny, nz, re_tau=1000.0, n_modes=100, uniforms=None, seed=1,
+                 precision="fp32", u_bulk=0.05, c_smag=0.01, kappa=0.4, B=7.8, ell_e=0.4,
+                 amp=1.0, k_ratio=1.01, beta_kmin=0.5, wall_model=True, inlet=True,
+                 stats_every=0, stream=None, device=None):
+        import torch
+        self._torch = torch
+        self.lib = _abi.lib()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.ncell = self.nx * self.ny * self.nz
+        self.device = torch.device(device if device is not None else "cuda")
+        if uniforms is None and n_modes > 0:
+            uniforms = stg_uniforms(n_modes, seed)
+        self._uni = (np.ascontiguousarray(uniforms, dtype=np.float64).reshape(-1)
+                     if n_modes > 0 else np.zeros(4))
+        if n_modes > 0 and self._uni.size != 4 * n_modes:
+            raise ValueError("uniforms must hold n_modes x 4 values")
+        grid = _abi.Grid(self.nx, self.ny, self.nz)
+        stg = _abi.StgParams(int(n_modes), float(k_ratio), float(beta_kmin), float(ell_e),
+                             float(amp), _dptr(self._uni))
+        opts = _abi.Opts()
+        self.lib.lbm_default_opts(ct.byref(opts))
+        opts.precision = _abi.PRECISIONS[precision]
+        opts.u_bulk, opts.c_smag, opts.kappa, opts.B = u_bulk, c_smag, kappa, B
+        opts.wall_model, opts.inlet, opts.stats_every = int(wall_model), int(inlet), int(stats_every)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        opts.cuda_stream = ct.c_void_p(stream.cuda_stream)
+        h = ct.c_void_p()
+        _abi.check(self.lib.lbm_create(ct.byref(grid), float(re_tau), ct.byref(stg), ct.byref(opts),
+                                       ct.byref(h)), "lbm_create")
+        self.h = h
+        nbytes = ct.c_size_t()
+        _abi.check(self.lib.lbm_required_bytes(self.h, ct.byref(nbytes)), "lbm_required_bytes")
+        self.nbytes = nbytes.value
+        with torch.cuda.device(self.device):
+            self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        _abi.check(self.lib.lbm_bind_memory(self.h, ct.c_void_p(self.mem.data_ptr()),
+                                            self.nbytes), "lbm_bind_memory")
+        self.precision = precision
+
+    # ---- life cycle ----
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_destroy(self.h)
+            self.h = None
+            self.mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- stepping ----
+    def step(self, n=1):
+        _abi.check(self.lib.lbm_step(self.h, int(n)), "lbm_step")
+
+    def sync(self):
+        _abi.check(self.lib.lbm_sync(self.h), "lbm_sync")
+
+    @property
+    def time(self):
+        t = ct.c_long()
+        _abi.check(self.lib.lbm_get_time(self.h, ct.byref(t)), "lbm_get_time")
+        return t.value
+
+    @time.setter
+    def time(self, t):
+        _abi.check(self.lib.lbm_set_time(self.h, int(t)), "lbm_set_time")
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        _abi.check(self.lib.lbm_set_params(self.h, _dptr(th)), "lbm_set_params")
+
+    # ---- host copies ----
+    def fields(self):
+        rho = np.empty((self.nz, self.ny, self.nx))
+        u = np.empty((self.nz, self.ny, self.nx, 3))
+        _abi.check(self.lib.lbm_get_fields(self.h, _dptr(rho), _dptr(u)), "lbm_get_fields")
+        return rho, u
+
+    def populations(self):
+        f = np.empty((Q, self.nz, self.ny, self.nx))
+        _abi.check(self.lib.lbm_get_populations(self.h, _dptr(f)), "lbm_get_populations")
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.size != Q * self.ncell:
+            raise ValueError("populations must be 19 x nz x ny x nx")
+        _abi.check(self.lib.lbm_set_populations(self.h, _dptr(f)), "lbm_set_populations")
+
+    def utau(self):
+        u = np.empty((2, self.nz, self.nx))
+        _abi.check(self.lib.lbm_get_utau(self.h, _dptr(u)), "lbm_get_utau")
+        return u
+
+    def inlet_velocity(self, t):
+        out = np.empty((self.nz, self.ny, 3))
+        _abi.check(self.lib.lbm_inlet_velocity(self.h, int(t), _dptr(out)), "lbm_inlet_velocity")
+        return out
+
+    def constants(self):
+        o = np.empty(6)
+        _abi.check(self.lib.lbm_get_constants(self.h, _dptr(o)), "lbm_get_constants")
+        return dict(delta=o[0], utau_ref=o[1], nu=o[2], tau0=o[3], ubp=o[4], maxl=o[5])
+
+    def stats(self):
+        s = np.empty((self.ny, self.nx, 7))
+        ut = np.empty((2, self.nx))
+        n = ct.c_long()
+        _abi.check(self.lib.lbm_stats(self.h, _dptr(s), _dptr(ut), ct.byref(n)), "lbm_stats")
+        return s, ut, n.value
+
+    def reset_stats(self):
+        _abi.check(self.lib.lbm_reset_stats(self.h), "lbm_reset_stats")

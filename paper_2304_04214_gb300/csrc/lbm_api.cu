@@ -1,0 +1,751 @@
+// lbm_api.cu -- host side of liblbm_gb300.so: the C ABI of include/lbm.h.
+//
+// The handle keeps the flow constants and the STG tables (built in FP64 on
+// the host, Algorithm 1 steps 1-3), carves one device arena into the two
+// lattices and the small buffers, and enqueues the kernels of
+// lbm_device.cuh on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_device.cuh"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Arena {
+    char *base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Host FP64 Reichardt law (Sec. 2.3 eq:reichard, textbook coefficients).
+double uplus(double yp, double kap, double B) {
+    return std::log1p(kap * yp) / kap + B * (1.0 - std::exp(-yp / 11.0) - yp / 11.0 * std::exp(-yp / 3.0));
+}
+
+// fractional turns -> 32-bit fixed point
+uint32_t turns32(double turns) {
+    double fr = turns - std::floor(turns);
+    double v = std::floor(fr * 4294967296.0 + 0.5);
+    if (v >= 4294967296.0) v -= 4294967296.0;
+    return (uint32_t)(uint64_t)v;
+}
+
+}  // namespace
+
+struct lbm_handle {
+    int nx = 0, ny = 0, nz = 0;
+    long long ncell = 0;
+    double re_tau = 0;
+    lbm_opts opts{};
+    int n_modes = 0;
+    double k_ratio = 1.01, beta_kmin = 0.5;
+    std::vector<double> uniforms;
+    double theta[4] = {0.4, 1.0, 0.4, 7.8};
+    // flow constants (fixed at creation)
+    double delta = 0, utau_ref = 0, nu = 0, tau0 = 0, ubp = 0, maxl = 0;
+    // host tables
+    std::vector<float> UR, amat, sq, sig;
+    std::vector<uint32_t> alpha, beta, phi32;
+    std::vector<uint64_t> rate64;
+    // device
+    bool bound = false, owns = false;
+    void *mem = nullptr;
+    size_t mem_bytes = 0;
+    void *lat[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *d_utau = nullptr, *d_fw = nullptr, *d_uin = nullptr, *d_ubuf = nullptr;
+    double *d_st = nullptr, *d_st_utau = nullptr;
+    long long *d_t = nullptr;
+    unsigned *d_flags = nullptr;
+    float *d_UR = nullptr, *d_amat = nullptr, *d_sq = nullptr, *d_sig = nullptr;
+    uint32_t *d_alpha = nullptr, *d_beta = nullptr, *d_phi32 = nullptr;
+    uint64_t *d_rate64 = nullptr;
+    cudaStream_t stream = nullptr;
+    long long t = 0;
+    long long steps_since_stats = 0;
+    long n_samples = 0;
+    long long t_host_buf = 0;
+    // inlet profile (RANS input of Algorithm 1 steps 1-3): U[j], R[6j..6j+5]
+    bool custom_profile = false;
+    std::vector<double> prof_U, prof_R;
+    double *d_tw = nullptr;                // [2][nx] wall-shear scratch
+    float *pin_stage = nullptr;            // pinned staging of U_R and amp*chol(R): 7*ny floats
+    cudaEvent_t stage_ev = nullptr;        // last upload from the staging buffer
+    // instrumentation
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev0, ev1;
+    std::vector<char> ev_busy;
+    size_t ev_next = 0;
+    double prof_ms = 0;
+    long prof_n = 0, launches = 0;
+    size_t elem = 4;
+
+    size_t layout(Arena &ar) {
+        const size_t N = (size_t)n_modes > 0 ? (size_t)n_modes : 1;
+        lat[0] = ar.take<char>(19 * (size_t)ncell * elem);
+        lat[1] = ar.take<char>(19 * (size_t)ncell * elem);
+        d_utau = ar.take<float>(2 * (size_t)nz * nx);
+        d_fw = ar.take<float>(6 * (size_t)nz * nx);
+        d_uin = ar.take<float>(3 * (size_t)nz * ny);
+        d_ubuf = opts.stats_every > 0 ? ar.take<float>(3 * (size_t)ncell) : nullptr;
+        d_st = ar.take<double>(7 * (size_t)nx * ny);
+        d_st_utau = ar.take<double>(2 * (size_t)nx);
+        d_t = ar.take<long long>(1);
+        d_tw = ar.take<double>(2 * (size_t)nx);
+        d_flags = ar.take<unsigned>(4);
+        d_UR = ar.take<float>(ny);
+        d_amat = ar.take<float>(6 * (size_t)ny);
+        d_sq = ar.take<float>((size_t)ny * N);
+        d_sig = ar.take<float>(3 * N);
+        d_alpha = ar.take<uint32_t>((size_t)ny * N);
+        d_beta = ar.take<uint32_t>((size_t)nz * N);
+        d_phi32 = ar.take<uint32_t>(N);
+        d_rate64 = ar.take<uint64_t>(N);
+        return (ar.off + 255) & ~size_t(255);
+    }
+
+    // Flow constants (A20): U_b+ = mean of u+ over the cell centres with the
+    // creation-time (kappa, B); u_tau = U_b / U_b+, nu = u_tau delta / Re_tau.
+    void constants() {
+        delta = 0.5 * ny;
+        double s = 0;
+        for (int j = 0; j < ny; ++j) s += uplus(dwall(j) * re_tau / delta, opts.kappa, opts.B);
+        ubp = s / ny;
+        utau_ref = opts.u_bulk / ubp;
+        nu = utau_ref * delta / re_tau;
+        tau0 = 3.0 * nu + 0.5;     // eq:nu with c_s^2 = 1/3
+    }
+    double dwall(int j) const { return std::min(j + 0.5, ny - j - 0.5); }
+
+    // Inlet tables: mean profile, Cholesky factor of the prescribed Reynolds
+    // stress (eq:cholesky), STG modes and spectrum (Sec. 3.1).
+    void tables() {
+        const double ell_e = theta[0], amp = theta[1], kap = theta[2], B = theta[3];
+        const int N = n_modes;
+        if (!custom_profile) {
+            prof_U.assign(ny, 0.0);
+            prof_R.assign(6 * (size_t)ny, 0.0);
+            for (int j = 0; j < ny; ++j) {
+                const double d = dwall(j);
+                prof_U[j] = utau_ref * uplus(d * utau_ref / nu, kap, B);
+                // prescribed stress in wall units: -uv+ = (1 - d/delta)(1 - e^{-d+/26})^2,
+                // normal stresses 3s + 0.1, s + 0.1, 2s + 0.1; sign of uv flips above the centre
+                const double e = 1.0 - std::exp(-d * re_tau / delta / 26.0);
+                const double sh = (1.0 - d / delta) * e * e;
+                const double u2 = utau_ref * utau_ref;
+                double *R = &prof_R[6 * (size_t)j];
+                R[0] = (3 * sh + 0.1) * u2; R[1] = (sh + 0.1) * u2; R[2] = (2 * sh + 0.1) * u2;
+                R[3] = ((j + 0.5) < 0.5 * ny ? -sh : sh) * u2; R[4] = 0.0; R[5] = 0.0;
+            }
+        }
+        profile_tables(amp);
+        const size_t NN = N > 0 ? N : 1;
+        sq.assign((size_t)ny * NN, 0.f);
+        sig.assign(3 * NN, 0.f);
+        alpha.assign((size_t)ny * NN, 0u);
+        beta.assign((size_t)nz * NN, 0u);
+        phi32.assign(NN, 0u);
+        rate64.assign(NN, 0ull);
+        if (N == 0) { maxl = 0; return; }
+        // l_e(y) = ell_e delta tanh(2 d / (ell_e delta)); largest at the centre rows
+        std::vector<double> ell(ny);
+        maxl = 0;
+        for (int j = 0; j < ny; ++j) {
+            ell[j] = ell_e * delta * std::tanh(2.0 * dwall(j) / (ell_e * delta));
+            maxl = std::max(maxl, ell[j]);
+        }
+        std::vector<double> kn(N), dx(N), dy(N), dz(N);
+        const double kmin = beta_kmin * 2.0 * kPi / maxl;
+        for (int n = 0; n < N; ++n) {
+            kn[n] = kmin * std::pow(k_ratio, n);
+            const double *U = &uniforms[4 * (size_t)n];
+            const double ct = 1.0 - 2.0 * U[0], st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+            const double az = 2.0 * kPi * U[1], ang = 2.0 * kPi * U[2];
+            dx[n] = st * std::cos(az); dy[n] = st * std::sin(az); dz[n] = ct;
+            // sigma_n: unit vector normal to d_n at angle ang from the polar direction
+            const double e1[3] = {ct * std::cos(az), ct * std::sin(az), -st};
+            const double e2[3] = {-std::sin(az), std::cos(az), 0.0};
+            for (int c = 0; c < 3; ++c)
+                sig[(size_t)c * N + n] = (float)(std::cos(ang) * e1[c] + std::sin(ang) * e2[c]);
+            phi32[n] = turns32(U[3]);
+            // time part of the phase: -(d_x U_b / max l_e) turns per step
+            const double nu_n = dx[n] * opts.u_bulk / maxl;
+            const long long fx = std::llround(-nu_n * 18446744073709551616.0);
+            rate64[n] = (uint64_t)fx;
+        }
+        for (int j = 0; j < ny; ++j)
+            for (int n = 0; n < N; ++n) alpha[(size_t)j * N + n] = turns32(kn[n] * dy[n] * (j + 0.5) / (2 * kPi));
+        for (int k = 0; k < nz; ++k)
+            for (int n = 0; n < N; ++n) beta[(size_t)k * N + n] = turns32(kn[n] * dz[n] * (k + 0.5) / (2 * kPi));
+        // q_n(y) from the modified von Karman spectrum with Kolmogorov and
+        // grid cut-offs; sqrt(6 q_n) stored (the sqrt6 of eq:aux_vec folded in)
+        const double kcut = kPi;                        // 2 pi / (2 dx)
+        std::vector<double> E(N);
+        for (int j = 0; j < ny; ++j) {
+            const double d = dwall(j), ke = 2.0 * kPi / ell[j];
+            const double eps = utau_ref * utau_ref * utau_ref / (opts_kappa0 * d);
+            const double keta = 2.0 * kPi * std::pow(eps / (nu * nu * nu), 0.25);
+            double tot = 0;
+            for (int n = 0; n < N; ++n) {
+                const double k = kn[n], r = k / ke;
+                const double dk = k * (1.0 - 1.0 / k_ratio);
+                const double xc = 4.0 * std::max(k - 0.9 * kcut, 0.0) / kcut;
+                E[n] = r * r * r * r / std::pow(1.0 + 2.4 * r * r, 17.0 / 6.0) *
+                       std::exp(-(12.0 * k / keta) * (12.0 * k / keta)) * std::exp(-xc * xc * xc) * dk;
+                tot += E[n];
+            }
+            for (int n = 0; n < N; ++n) sq[(size_t)j * N + n] = (float)std::sqrt(6.0 * E[n] / tot);
+        }
+    }
+    double opts_kappa0 = 0.4;   // the creation-time kappa (dissipation estimate of the spectrum)
+
+    // U_R and amp * chol(R) per row (eq:cholesky); false if R is not SPD
+    bool profile_tables(double amp) {
+        UR.assign(ny, 0.f);
+        amat.assign(6 * (size_t)ny, 0.f);
+        for (int j = 0; j < ny; ++j) {
+            const double *R = &prof_R[6 * (size_t)j];   // 11, 22, 33, 12, 13, 23
+            const double r11 = R[0], r22 = R[1], r33 = R[2], r21 = R[3], r31 = R[4], r32 = R[5];
+            if (!(r11 > 0)) return false;
+            const double l11 = std::sqrt(r11);
+            const double l21 = r21 / l11, l31 = r31 / l11;
+            const double p22 = r22 - l21 * l21;
+            if (!(p22 > 0)) return false;
+            const double l22 = std::sqrt(p22);
+            const double l32 = (r32 - l21 * l31) / l22;
+            const double p33 = r33 - l31 * l31 - l32 * l32;
+            if (!(p33 > 0)) return false;
+            const double L[6] = {l11, l21, l22, l31, l32, std::sqrt(p33)};
+            UR[j] = (float)prof_U[j];
+            for (int c = 0; c < 6; ++c) amat[6 * (size_t)j + c] = (float)(amp * L[c]);
+        }
+        return true;
+    }
+
+    cudaError_t upload_tables() {
+        const size_t N = n_modes > 0 ? n_modes : 1;
+        cudaError_t e;
+#define UP(dst, vec) if ((e = cudaMemcpyAsync(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return e
+        UP(d_UR, UR); UP(d_amat, amat); UP(d_sq, sq); UP(d_sig, sig);
+        UP(d_alpha, alpha); UP(d_beta, beta); UP(d_phi32, phi32); UP(d_rate64, rate64);
+#undef UP
+        (void)N;
+        return cudaStreamSynchronize(stream);   // host vectors may change after return
+    }
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    std::fprintf(stderr, "liblbm_gb300: CUDA error: %s\n", cudaGetErrorString(e));
+    return LBM_ECUDA;
+}
+
+constexpr size_t kEventPool = 2048;
+
+// Harvest a finished event pair into the running total.
+void prof_harvest(lbm_handle *h, size_t slot) {
+    if (!h->ev_busy[slot]) return;
+    float ms = 0.f;
+    cudaEventSynchronize(h->ev1[slot]);
+    cudaEventElapsedTime(&ms, h->ev0[slot], h->ev1[slot]);
+    h->prof_ms += ms;
+    h->prof_n += 1;
+    h->ev_busy[slot] = 0;
+}
+
+size_t prof_slot(lbm_handle *h) {
+    const size_t slot = h->ev_next;
+    h->ev_next = (h->ev_next + 1) % kEventPool;
+    prof_harvest(h, slot);
+    h->ev_busy[slot] = 1;
+    return slot;
+}
+
+template <class S>
+void launch_step_t(lbm_handle *h, bool stats) {
+    using T = typename S::T;
+    lbmk::StepArgs<S> a;
+    a.fin = (const T *)h->lat[h->cur];
+    a.fout = (T *)h->lat[h->cur ^ 1];
+    a.uin = h->d_uin;
+    a.utau = h->d_utau;
+    a.fw = h->d_fw;
+    a.ubuf = h->d_ubuf;
+    a.flags = h->d_flags;
+    a.t_dev = h->d_t;
+    a.ncell = h->ncell;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    a.inlet = h->opts.inlet; a.wall_model = h->opts.wall_model;
+    a.tau0 = (float)h->tau0;
+    a.csm18 = (float)(18.0 * std::sqrt(2.0) * h->opts.c_smag);
+    a.y1_nu = (float)(0.5 / h->nu);
+    a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
+    const int bx = h->nx >= 64 ? 64 : 32;
+    dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
+    const size_t slot = h->prof_on ? prof_slot(h) : 0;
+    if (h->prof_on) cudaEventRecord(h->ev0[slot], h->stream);
+    if (stats) lbmk::step_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
+    else lbmk::step_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
+    if (h->prof_on) cudaEventRecord(h->ev1[slot], h->stream);
+    h->launches += 1;
+}
+
+void launch_stg(lbm_handle *h, const long long *t_dev, long long t_val) {
+    lbmk::StgArgs a;
+    a.alpha = h->d_alpha; a.beta = h->d_beta; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
+    a.sq = h->d_sq; a.sig = h->d_sig; a.amat = h->d_amat; a.UR = h->d_UR; a.uin = h->d_uin;
+    a.t_dev = t_dev; a.t_val = t_val;
+    a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
+    const int cells = h->ny * h->nz;
+    const int blocks = (cells * 32 + 255) / 256;
+    lbmk::stg_kernel<<<blocks, 256, 0, h->stream>>>(a);
+    h->launches += 1;
+}
+
+int one_step(lbm_handle *h) {
+    bool stats = false;
+    if (h->opts.stats_every > 0) {
+        h->steps_since_stats += 1;
+        if (h->steps_since_stats >= h->opts.stats_every) { stats = true; h->steps_since_stats = 0; }
+    }
+    if (h->opts.inlet) launch_stg(h, h->d_t, 0);
+    switch (h->opts.precision) {
+        case LBM_FP16_DEV: launch_step_t<lbmk::StoreF16>(h, stats); break;
+        case LBM_BF16_DEV: launch_step_t<lbmk::StoreBF16>(h, stats); break;
+        default: launch_step_t<lbmk::StoreF32>(h, stats); break;
+    }
+    if (stats) {
+        h->n_samples += 1;
+        const int n = h->nx * h->ny + 2 * h->nx;
+        lbmk::stats_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(
+            h->d_ubuf, h->d_utau, h->d_st, h->d_st_utau, h->nx, h->ny, h->nz, h->ncell, h->opts.wall_model);
+        h->launches += 1;
+    }
+    h->cur ^= 1;
+    h->t += 1;
+    return cuda_fail(cudaGetLastError());
+}
+
+template <class S>
+void launch_init(lbm_handle *h, void *lat) {
+    const long long n = h->ncell;
+    lbmk::init_kernel<S><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>((typename S::T *)lat, h->d_UR,
+                                                                               h->nx, h->ny, n);
+}
+
+const double kW[19] = {1. / 36, 1. / 36, 1. / 18, 1. / 36, 1. / 36, 1. / 36, 1. / 18, 1. / 36, 1. / 18, 1. / 3,
+                       1. / 18, 1. / 36, 1. / 18, 1. / 36, 1. / 36, 1. / 36, 1. / 18, 1. / 36, 1. / 36};
+
+uint16_t f32_to_bf16_rn(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    if ((b & 0x7f800000u) == 0x7f800000u) return (uint16_t)(b >> 16);   // inf / nan
+    b += 0x7fffu + ((b >> 16) & 1u);
+    return (uint16_t)(b >> 16);
+}
+float bf16_to_f32(uint16_t v) {
+    uint32_t b = (uint32_t)v << 16;
+    float x;
+    std::memcpy(&x, &b, 4);
+    return x;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_opts(lbm_opts *o) {
+    if (!o) return;
+    o->precision = LBM_FP32;
+    o->u_bulk = 0.05;
+    o->c_smag = 0.01;
+    o->kappa = 0.4;
+    o->B = 7.8;
+    o->wall_model = 1;
+    o->inlet = 1;
+    o->stats_every = 0;
+    o->cuda_stream = nullptr;
+}
+
+int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg, const lbm_opts *opts,
+               lbm_handle **out) {
+    if (!grid || !stg || !opts || !out) return LBM_EINVAL;
+    *out = nullptr;
+    if (grid->ny < 4 || grid->ny % 2 || grid->nx < 3 || grid->nz < 1) return LBM_EINVAL;
+    if ((long long)grid->nx * grid->ny * grid->nz >= (1ll << 31)) return LBM_EINVAL;
+    if (!(re_tau > 0) || stg->n_modes < 0 || (stg->n_modes > 0 && !stg->uniforms)) return LBM_EINVAL;
+    if (opts->precision < LBM_FP32 || opts->precision > LBM_BF16_DEV) return LBM_EINVAL;
+    if (!(opts->u_bulk > 0) || !(opts->kappa > 0) || opts->stats_every < 0) return LBM_EINVAL;
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ENOMEM;
+    h->nx = grid->nx; h->ny = grid->ny; h->nz = grid->nz;
+    h->ncell = (long long)h->nx * h->ny * h->nz;
+    h->re_tau = re_tau;
+    h->opts = *opts;
+    h->stream = (cudaStream_t)opts->cuda_stream;
+    h->n_modes = stg->n_modes;
+    h->k_ratio = stg->k_ratio;
+    h->beta_kmin = stg->beta_kmin;
+    h->uniforms.assign(stg->uniforms ? stg->uniforms : nullptr,
+                       stg->uniforms ? stg->uniforms + 4 * (size_t)stg->n_modes : nullptr);
+    h->theta[0] = stg->ell_e; h->theta[1] = stg->amp; h->theta[2] = opts->kappa; h->theta[3] = opts->B;
+    h->opts_kappa0 = opts->kappa;
+    h->elem = opts->precision == LBM_FP32 ? 4 : 2;
+    h->constants();
+    h->tables();
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_required_bytes(const lbm_handle *h, size_t *bytes) {
+    if (!h || !bytes) return LBM_EINVAL;
+    Arena ar;
+    lbm_handle tmp_view = *h;   // layout() only writes pointers of the copy
+    *bytes = tmp_view.layout(ar);
+    return LBM_OK;
+}
+
+int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
+    if (!h) return LBM_EINVAL;
+    if (h->bound) return LBM_ESTATE;
+    size_t need = 0;
+    lbm_required_bytes(h, &need);
+    if (dev_ptr) {
+        if (((uintptr_t)dev_ptr & 255) != 0) return LBM_EINVAL;
+        if (bytes < need) return LBM_ENOMEM;
+        h->mem = dev_ptr;
+        h->owns = false;
+    } else {
+        if (cudaMalloc(&h->mem, need) != cudaSuccess) { cudaGetLastError(); return LBM_ENOMEM; }
+        h->owns = true;
+    }
+    h->mem_bytes = need;
+    if (cudaHostAlloc((void **)&h->pin_stage, 7 * sizeof(float) * h->ny, cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+        if (h->owns) cudaFree(h->mem);
+        h->mem = nullptr;
+        return cuda_fail(cudaGetLastError());
+    }
+    Arena ar;
+    ar.base = (char *)h->mem;
+    h->layout(ar);
+    h->bound = true;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->mem, 0, need, h->stream)) != cudaSuccess) return cuda_fail(e);
+    if ((e = h->upload_tables()) != cudaSuccess) return cuda_fail(e);
+    std::vector<float> ut(2 * (size_t)h->nz * h->nx, (float)h->utau_ref);
+    if ((e = cudaMemcpyAsync(h->d_utau, ut.data(), ut.size() * 4, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    switch (h->opts.precision) {
+        case LBM_FP16_DEV: launch_init<lbmk::StoreF16>(h, h->lat[0]); break;
+        case LBM_BF16_DEV: launch_init<lbmk::StoreBF16>(h, h->lat[0]); break;
+        default: launch_init<lbmk::StoreF32>(h, h->lat[0]); break;
+    }
+    h->cur = 0;
+    h->t = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    return cuda_fail(cudaStreamSynchronize(h->stream));
+}
+
+int lbm_step(lbm_handle *h, int n) {
+    if (!h || n < 0) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    for (int s = 0; s < n; ++s) {
+        int rc = one_step(h);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle *h) {
+    if (!h) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    unsigned fl[2] = {0, 0};
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(fl, h->d_flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
+    if (fl[0] || fl[1]) {
+        if ((e = cudaMemsetAsync(h->d_flags, 0, sizeof fl, h->stream)) != cudaSuccess) return cuda_fail(e);
+        cudaStreamSynchronize(h->stream);
+    }
+    if (fl[1]) return LBM_EDIVERGED;
+    if (fl[0]) return LBM_ENOTCONV;
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle *h, void *s) {
+    if (!h) return LBM_EINVAL;
+    h->stream = (cudaStream_t)s;
+    h->opts.cuda_stream = s;
+    return LBM_OK;
+}
+
+int lbm_stats(lbm_handle *h, double *sums, double *utau_sums, long *n_samples) {
+    if (!h || !sums || !utau_sums || !n_samples) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(sums, h->d_st, 7 * sizeof(double) * h->nx * h->ny, cudaMemcpyDeviceToHost,
+                             h->stream)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(utau_sums, h->d_st_utau, 2 * sizeof(double) * h->nx, cudaMemcpyDeviceToHost,
+                             h->stream)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
+    *n_samples = h->n_samples;
+    return LBM_OK;
+}
+
+int lbm_reset_stats(lbm_handle *h) {
+    if (!h) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->d_st, 0, 7 * sizeof(double) * h->nx * h->ny, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemsetAsync(h->d_st_utau, 0, 2 * sizeof(double) * h->nx, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    h->steps_since_stats = 0;
+    h->n_samples = 0;
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_handle *h, double *rho, double *u) {
+    if (!h || !rho || !u) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    // the other lattice is free between steps: use it as scratch (>= 16 B per cell)
+    float *drho = (float *)h->lat[h->cur ^ 1];
+    float *du = drho + h->ncell;
+    const long long n = h->ncell;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    h->launches += 1;
+    switch (h->opts.precision) {
+        case LBM_FP16_DEV:
+            lbmk::fields_kernel<lbmk::StoreF16><<<blocks, 256, 0, h->stream>>>(
+                (const __half *)h->lat[h->cur], h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
+            break;
+        case LBM_BF16_DEV:
+            lbmk::fields_kernel<lbmk::StoreBF16><<<blocks, 256, 0, h->stream>>>(
+                (const __nv_bfloat16 *)h->lat[h->cur], h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
+            break;
+        default:
+            lbmk::fields_kernel<lbmk::StoreF32><<<blocks, 256, 0, h->stream>>>(
+                (const float *)h->lat[h->cur], h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
+    }
+    cudaError_t e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    std::vector<float> buf(4 * (size_t)n);
+    if ((e = cudaMemcpyAsync(buf.data(), drho, 4 * sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream)) !=
+        cudaSuccess) return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
+    for (long long c = 0; c < n; ++c) rho[c] = buf[c];
+    for (long long c = 0; c < 3 * n; ++c) u[c] = buf[n + c];
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_handle *h, double *f) {
+    if (!h || !f) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    const size_t n = 19 * (size_t)h->ncell;
+    std::vector<char> buf(n * h->elem);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(buf.data(), h->lat[h->cur], n * h->elem, cudaMemcpyDeviceToHost, h->stream)) !=
+        cudaSuccess) return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
+    const size_t N = h->ncell;
+    for (size_t idx = 0; idx < n; ++idx) {
+        const int q = (int)(idx / N);
+        if (h->opts.precision == LBM_FP32) f[idx] = ((const float *)buf.data())[idx];
+        else if (h->opts.precision == LBM_FP16_DEV)
+            f[idx] = kW[q] + (double)__half2float(((const __half *)buf.data())[idx]);
+        else f[idx] = kW[q] + (double)bf16_to_f32(((const uint16_t *)buf.data())[idx]);
+    }
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_handle *h, const double *f) {
+    if (!h || !f) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    const size_t n = 19 * (size_t)h->ncell, N = h->ncell;
+    std::vector<char> buf(n * h->elem);
+    for (size_t idx = 0; idx < n; ++idx) {
+        const int q = (int)(idx / N);
+        if (h->opts.precision == LBM_FP32) ((float *)buf.data())[idx] = (float)f[idx];
+        else if (h->opts.precision == LBM_FP16_DEV)
+            ((__half *)buf.data())[idx] = __double2half(f[idx] - kW[q]);
+        else ((uint16_t *)buf.data())[idx] = f32_to_bf16_rn((float)(f[idx] - kW[q]));
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->lat[h->cur], buf.data(), n * h->elem, cudaMemcpyHostToDevice, h->stream)) !=
+        cudaSuccess) return cuda_fail(e);
+    return cuda_fail(cudaStreamSynchronize(h->stream));
+}
+
+int lbm_get_utau(lbm_handle *h, double *utau) {
+    if (!h || !utau) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    const size_t n = 2 * (size_t)h->nz * h->nx;
+    std::vector<float> buf(n);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(buf.data(), h->d_utau, n * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
+    for (size_t c = 0; c < n; ++c) utau[c] = buf[c];
+    return LBM_OK;
+}
+
+int lbm_get_time(const lbm_handle *h, long *t) {
+    if (!h || !t) return LBM_EINVAL;
+    *t = (long)h->t;
+    return LBM_OK;
+}
+
+int lbm_set_time(lbm_handle *h, long t) {
+    if (!h || t < 0) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    h->t = t;
+    h->t_host_buf = t;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->d_t, &h->t_host_buf, sizeof(long long), cudaMemcpyHostToDevice, h->stream)) !=
+        cudaSuccess) return cuda_fail(e);
+    return cuda_fail(cudaStreamSynchronize(h->stream));
+}
+
+int lbm_get_constants(const lbm_handle *h, double out[6]) {
+    if (!h || !out) return LBM_EINVAL;
+    out[0] = h->delta; out[1] = h->utau_ref; out[2] = h->nu; out[3] = h->tau0; out[4] = h->ubp; out[5] = h->maxl;
+    return LBM_OK;
+}
+
+int lbm_inlet_velocity(lbm_handle *h, long t, double *out) {
+    if (!h || !out || t < 0) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    launch_stg(h, nullptr, t);
+    cudaError_t e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    const size_t n = 3 * (size_t)h->ny * h->nz;
+    std::vector<float> buf(n);
+    if ((e = cudaMemcpyAsync(buf.data(), h->d_uin, n * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
+    for (size_t c = 0; c < n; ++c) out[c] = buf[c];
+    return LBM_OK;
+}
+
+int lbm_set_params(lbm_handle *h, const double theta[4]) {
+    if (!h || !theta) return LBM_EINVAL;
+    if (!(theta[0] > 0) || !(theta[2] > 0)) return LBM_EINVAL;
+    for (int c = 0; c < 4; ++c) h->theta[c] = theta[c];
+    h->tables();
+    if (!h->bound) return LBM_OK;
+    return cuda_fail(h->upload_tables());
+}
+
+int lbm_set_inlet_profile(lbm_handle *h, const double *U, const double *R) {
+    if (!h || !U || !R) return LBM_EINVAL;
+    std::vector<double> oldU = h->prof_U, oldR = h->prof_R;
+    h->prof_U.assign(U, U + h->ny);
+    h->prof_R.assign(R, R + 6 * (size_t)h->ny);
+    if (!h->profile_tables(h->theta[1])) {
+        h->prof_U = oldU; h->prof_R = oldR;
+        h->profile_tables(h->theta[1]);
+        return LBM_EINVAL;
+    }
+    h->custom_profile = true;
+    if (!h->bound) return LBM_OK;
+    cudaError_t e;
+    // the pinned staging buffer may still feed the previous upload
+    if ((e = cudaEventSynchronize(h->stage_ev)) != cudaSuccess) return cuda_fail(e);
+    std::copy(h->UR.begin(), h->UR.end(), h->pin_stage);
+    std::copy(h->amat.begin(), h->amat.end(), h->pin_stage + h->ny);
+    // d_UR and d_amat are adjacent in the arena only up to alignment: two copies
+    if ((e = cudaMemcpyAsync(h->d_UR, h->pin_stage, h->ny * 4, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(h->d_amat, h->pin_stage + h->ny, 6 * h->ny * 4, cudaMemcpyHostToDevice,
+                             h->stream)) != cudaSuccess) return cuda_fail(e);
+    return cuda_fail(cudaEventRecord(h->stage_ev, h->stream));
+}
+
+int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R) {
+    if (!h || !U || !R) return LBM_EINVAL;
+    std::copy(h->prof_U.begin(), h->prof_U.end(), U);
+    std::copy(h->prof_R.begin(), h->prof_R.end(), R);
+    return LBM_OK;
+}
+
+int lbm_wall_shear(lbm_handle *h, double *out) {
+    if (!h || !out) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    const int n = 2 * h->nx;
+    lbmk::wall_shear_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(h->d_fw, h->d_tw, h->nx, h->nz);
+    h->launches += 1;
+    cudaError_t e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(out, h->d_tw, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    return cuda_fail(cudaStreamSynchronize(h->stream));
+}
+
+int lbm_profile_enable(lbm_handle *h, int on) {
+    if (!h) return LBM_EINVAL;
+    if (on && h->ev0.empty()) {
+        h->ev0.resize(kEventPool); h->ev1.resize(kEventPool); h->ev_busy.assign(kEventPool, 0);
+        for (size_t c = 0; c < kEventPool; ++c) {
+            if (cudaEventCreate(&h->ev0[c]) != cudaSuccess || cudaEventCreate(&h->ev1[c]) != cudaSuccess)
+                return cuda_fail(cudaGetLastError());
+        }
+    }
+    h->prof_on = on != 0;
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_handle *h, double *ms_total, long *step_launches, long *all_launches) {
+    if (!h || !ms_total || !step_launches || !all_launches) return LBM_EINVAL;
+    for (size_t c = 0; c < h->ev_busy.size(); ++c) prof_harvest(h, c);
+    *ms_total = h->prof_ms;
+    *step_launches = h->prof_n;
+    *all_launches = h->launches;
+    h->prof_ms = 0;
+    h->prof_n = 0;
+    h->launches = 0;
+    return cuda_fail(cudaGetLastError());
+}
+
+void lbm_destroy(lbm_handle *h) {
+    if (!h) return;
+    if (h->bound) cudaStreamSynchronize(h->stream);
+    for (size_t c = 0; c < h->ev0.size(); ++c) { cudaEventDestroy(h->ev0[c]); cudaEventDestroy(h->ev1[c]); }
+    if (h->owns && h->mem) cudaFree(h->mem);
+    if (h->pin_stage) cudaFreeHost(h->pin_stage);
+    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    delete h;
+}
+
+const char *lbm_error_string(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument";
+        case LBM_ENOMEM: return "not enough device memory";
+        case LBM_ECUDA: return "CUDA runtime error";
+        case LBM_EDIVERGED: return "lattice diverged (non-finite or |u| > 0.3)";
+        case LBM_ENOTCONV: return "u_tau Newton solve did not converge";
+        case LBM_ESTATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

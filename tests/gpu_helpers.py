@@ -1,0 +1,49 @@
+"""Shared set-up of the GPU parity tests: one oracle and one CUDA channel built
+from the same seeded inputs, and the error measures the tolerances refer to."""
+import numpy as np
+
+from oracle.oracle import Oracle, cell_api, default_config
+from paper_2304_04214_gb300.inputs import round_to_bf16, round_to_fp16, stg_uniforms
+
+Q = 19
+
+
+def make_pair(nx, ny, nz, re_tau=1000.0, n_modes=16, seed=1, precision="fp32", inlet=1,
+              wall_model=1, c_smag=0.01, theta=(0.4, 1.0, 0.4, 7.8), stats=0):
+    from paper_2304_04214_gb300.channel import LBMChannel
+    un = stg_uniforms(n_modes, seed) if n_modes > 0 else None
+    cfg = default_config(nx, ny, nz, re_tau=re_tau, n_modes=n_modes, inlet=inlet,
+                         wall_model=wall_model, c_smag=c_smag, stats=stats)
+    o = Oracle(cfg, theta=theta, uniforms=un)
+    g = LBMChannel(nx, ny, nz, re_tau=re_tau, n_modes=n_modes, uniforms=un, precision=precision,
+                   inlet=bool(inlet), wall_model=bool(wall_model), c_smag=c_smag,
+                   ell_e=theta[0], amp=theta[1], kappa=theta[2], B=theta[3],
+                   stats_every=1 if stats else 0)
+    return o, g
+
+
+def quantize_state(f, precision):
+    """Round the deviations f - w to the storage type, so that both sides
+    start from the same exactly representable state."""
+    if precision == "fp32":
+        return f.astype(np.float32).astype(np.float64)
+    _, w, _ = cell_api.matrix()
+    wq = w[:, None, None, None]
+    r = round_to_fp16 if precision == "fp16" else round_to_bf16
+    return wq + r(f - wq)
+
+
+def set_both(o, g, f):
+    f = quantize_state(f, g.precision)
+    o.set_state(f)
+    g.set_populations(f)
+    return f
+
+
+def field_errors(o, g):
+    """Max-norm errors of rho and u normalized by the oracle's max |.|."""
+    ro, uo = o.fields()
+    rg, ug = g.fields()
+    er = np.max(np.abs(rg - ro)) / np.max(np.abs(ro))
+    eu = np.max(np.abs(ug - uo)) / np.max(np.abs(uo))
+    return er, eu

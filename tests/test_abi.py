@@ -1,0 +1,91 @@
+"""The C-ABI library builds, loads and exports what include/lbm.h declares;
+host-side argument checks work without a GPU (no device call is made)."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2304_04214_gb300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _abi.lib()
+    names = declared_functions()
+    assert "lbm_step" in names and "lbm_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding declares every one of them, and nothing the header lacks
+    assert set(_abi.PROTOTYPES) == set(names)
+
+
+def test_error_strings():
+    lib = _abi.lib()
+    for code in (0, -1, -2, -3, -4, -5, -6, -99):
+        assert isinstance(lib.lbm_error_string(code), bytes)
+    assert lib.lbm_error_string(-1) == b"invalid argument"
+
+
+def _create(nx=16, ny=8, nz=4, re_tau=1000.0, n_modes=4, uniforms=True, precision=0):
+    lib = _abi.lib()
+    un = np.full(4 * max(n_modes, 1), 0.25)
+    g = _abi.Grid(nx, ny, nz)
+    stg = _abi.StgParams(n_modes, 1.01, 0.5, 0.4, 1.0,
+                         un.ctypes.data_as(ct.POINTER(ct.c_double)) if uniforms else None)
+    o = _abi.Opts()
+    lib.lbm_default_opts(ct.byref(o))
+    o.precision = precision
+    h = ct.c_void_p()
+    rc = lib.lbm_create(ct.byref(g), re_tau, ct.byref(stg), ct.byref(o), ct.byref(h))
+    return rc, h
+
+
+def test_create_validates_arguments_on_the_host():
+    lib = _abi.lib()
+    for kw in (dict(ny=7), dict(ny=2), dict(nx=2), dict(nz=0), dict(re_tau=0.0), dict(n_modes=-1),
+               dict(uniforms=False), dict(precision=5)):
+        rc, h = _create(**kw)
+        assert rc == _abi.LBM_EINVAL, kw
+        assert not h.value
+    rc, h = _create()
+    assert rc == 0 and h.value
+    nb = ct.c_size_t()
+    assert lib.lbm_required_bytes(h, ct.byref(nb)) == 0
+    # two FP32 lattices dominate: 2 * 19 * ncell * 4 bytes
+    assert nb.value >= 2 * 19 * 16 * 8 * 4 * 4
+    c = np.empty(6)
+    assert lib.lbm_get_constants(h, c.ctypes.data_as(ct.POINTER(ct.c_double))) == 0
+    assert c[0] == 4.0 and c[1] > 0 and c[3] > 0.5
+    # calls that need device memory refuse before binding
+    assert lib.lbm_step(h, 1) == _abi.LBM_ESTATE
+    assert lib.lbm_step(h, -1) == _abi.LBM_EINVAL
+    assert lib.lbm_sync(h) == _abi.LBM_ESTATE
+    lib.lbm_destroy(h)
+
+
+def test_half_storage_needs_half_the_lattice_bytes():
+    lib = _abi.lib()
+    sizes = []
+    for p in (0, 1, 2):
+        rc, h = _create(nx=64, ny=32, nz=32, precision=p)
+        assert rc == 0
+        nb = ct.c_size_t()
+        lib.lbm_required_bytes(h, ct.byref(nb))
+        sizes.append(nb.value)
+        lib.lbm_destroy(h)
+    assert sizes[1] == sizes[2]
+    lat32, lat16 = 2 * 19 * 65536 * 4, 2 * 19 * 65536 * 2
+    assert sizes[0] - sizes[1] == pytest.approx(lat32 - lat16, abs=1024)

@@ -1,0 +1,164 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (max-norm error normalized by the oracle's max |.|):
+  FP32 storage  1e-5 after one step, 1e-3 after 200 steps.
+  FP16 deviations: the stored deviation f - w (|f - w| <~ 5e-3) carries a
+    relative rounding error of 2^-11, i.e. <~ 2.5e-6 absolute per population;
+    summed over the ten populations that make up a velocity component this is
+    <~ 2.5e-5 absolute against |u| ~ 0.06, so 1e-3 after one step.
+  BF16 deviations: 2^-8 relative, eight times more: 8e-3 after one step.
+  Over n steps the rounding errors add like a random walk: the half-precision
+    tolerances grow with sqrt(n) (x 14 at 200 steps).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import field_errors, make_pair, set_both
+from paper_2304_04214_gb300.inputs import noise
+
+pytestmark = pytest.mark.gpu
+
+TOL1 = {"fp32": 1e-5, "fp16": 1e-3, "bf16": 8e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("shape", [(64, 32, 32), (70, 16, 6)])
+def test_first_step_from_the_library_init(shape):
+    """Each side builds its own tables and initial state; one step agrees."""
+    o, g = make_pair(*shape, n_modes=32, seed=3)
+    o.step(1)
+    g.step(1)
+    er, eu = field_errors(o, g)
+    assert er < 1e-5 and eu < 1e-5, (er, eu)
+    ut_o, ut_g = o.utau(), g.utau()
+    assert np.max(np.abs(ut_g - ut_o)) < 1e-5 * np.max(ut_o)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("inlet", [1, 0])
+def test_one_step_perturbed_state(precision, inlet):
+    """Non-equilibrium state (2% noise on every population): every term of the
+    collision, the SGS closure, the wall model and the inlet is active."""
+    nx, ny, nz = 70, 16, 6
+    o, g = make_pair(nx, ny, nz, n_modes=24, seed=4, precision=precision, inlet=inlet)
+    f0 = o.state() * (1.0 + 0.02 * noise((19, nz, ny, nx), seed=11))
+    set_both(o, g, f0)
+    o.step(1)
+    g.step(1)
+    er, eu = field_errors(o, g)
+    tol = TOL1[precision]
+    assert er < tol and eu < tol, (precision, er, eu)
+    fo, fg = o.state(), g.populations()
+    # populations themselves, normalized by the largest deviation from w
+    dev = np.max(np.abs(fo - fo.mean(axis=(1, 2, 3), keepdims=True)))
+    assert np.max(np.abs(fg - fo)) < tol * max(dev, 1e-3) * 10
+
+
+def test_200_steps_small_channel():
+    """64x32x32 lattice, Re_tau = 1000, N = 100 modes, 200 steps, FP32."""
+    o, g = make_pair(64, 32, 32, n_modes=100, seed=1)
+    set_both(o, g, o.state())
+    o.step(200)
+    g.step(200)
+    g.sync()
+    er, eu = field_errors(o, g)
+    assert er < 1e-3 and eu < 1e-3, (er, eu)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_half_storage_200_steps(precision):
+    o, g = make_pair(64, 32, 32, n_modes=100, seed=1, precision=precision)
+    set_both(o, g, o.state())
+    o.step(200)
+    g.step(200)
+    er, eu = field_errors(o, g)
+    tol = TOL1[precision] * math.sqrt(200)
+    assert er < tol and eu < tol, (precision, er, eu)
+
+
+@pytest.mark.parametrize("t", [0, 7, 20000, 1234567])
+def test_stg_inlet_velocity(t):
+    o, g = make_pair(8, 48, 16, n_modes=200, seed=2)
+    uo = o.inlet_velocity(t)
+    ug = g.inlet_velocity(t)
+    UR = o.tables()["UR"]
+    fo = uo.copy()
+    fo[..., 0] -= UR[None, :]
+    assert np.max(np.abs(ug - uo)) < 1e-4 * np.max(np.abs(fo))
+
+
+def test_stg_amplitude_and_length_scale_parameters():
+    theta = (0.3, 1.7, 0.41, 7.1)
+    o, g = make_pair(8, 32, 8, n_modes=64, seed=6, theta=theta)
+    uo, ug = o.inlet_velocity(50), g.inlet_velocity(50)
+    assert np.max(np.abs(ug - uo)) < 1e-4 * np.max(np.abs(uo[..., 1:]))
+    # set_params rebuilds the tables
+    g.set_params((0.4, 1.0, 0.4, 7.8))
+    o2, _ = make_pair(8, 32, 8, n_modes=64, seed=6)
+    assert np.max(np.abs(g.inlet_velocity(50) - o2.inlet_velocity(50))) < 1e-4 * 0.01
+
+
+@pytest.mark.parametrize("shape,kw", [
+    ((3, 4, 1), {}),
+    ((5, 6, 2), {"n_modes": 0}),
+    ((33, 8, 3), {"wall_model": 0}),
+    ((40, 10, 4), {"inlet": 0, "n_modes": 0}),
+    ((129, 12, 5), {"c_smag": 0.0}),
+])
+def test_edge_cases(shape, kw):
+    args = dict(n_modes=8, seed=7)
+    args.update(kw)
+    o, g = make_pair(*shape, **args)
+    nx, ny, nz = shape
+    f0 = o.state() * (1.0 + 0.01 * noise((19, nz, ny, nx), seed=12))
+    set_both(o, g, f0)
+    o.step(3)
+    g.step(3)
+    er, eu = field_errors(o, g)
+    assert er < 1e-5 and eu < 1e-5, (shape, kw, er, eu)
+
+
+def test_statistics_accumulate_like_the_oracle():
+    o, g = make_pair(32, 16, 8, n_modes=16, seed=8, stats=1)
+    set_both(o, g, o.state())
+    o.step(10)
+    g.step(10)
+    so, uto, no = o.stats()
+    sg, utg, ng = g.stats()
+    assert no == ng == 10
+    for c in range(7):
+        assert np.max(np.abs(sg[..., c] - so[..., c])) < 1e-5 * np.max(np.abs(so[..., c])) + 1e-12, c
+    assert np.max(np.abs(utg - uto)) < 1e-5 * np.max(uto)
+
+
+def test_full_size_re_tau_1000_channel_first_steps():
+    """384x96x96 (Re_tau = 1000, N = 200): the bench workload and launch
+    configuration, compared over the whole lattice after two steps."""
+    o, g = make_pair(384, 96, 96, n_modes=200, seed=2)
+    o.step(2)
+    g.step(2)
+    er, eu = field_errors(o, g)
+    assert er < 1e-5 and eu < 1e-5, (er, eu)
+
+
+def test_divergence_is_reported():
+    """An unphysical state (|u| > 0.3) sets the device divergence flag, which
+    lbm_sync returns as LBM_EDIVERGED."""
+    from paper_2304_04214_gb300 import _abi
+    o, g = make_pair(16, 8, 4, n_modes=0)
+    f = o.state()
+    f[10] += 0.5          # a strong +x population everywhere
+    g.set_populations(f)
+    g.step(1)
+    with pytest.raises(_abi.LBMError) as e:
+        g.sync()
+    assert e.value.code == _abi.LBM_EDIVERGED
+    g.sync()              # the flag is cleared once reported
