@@ -79,9 +79,11 @@ def lib():
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build.LIB
-    if not os.path.exists(path) or _build._stale():
-        _build.build()
+    path = os.environ.get("LBM_GB300_LIB")       # an alternative build of the same sources
+    if not path:
+        path = _build.LIB
+        if not os.path.exists(path) or _build._stale():
+            _build.build()
     L = ct.CDLL(path)
     for name, (res, args) in PROTOTYPES.items():
         fn = getattr(L, name)

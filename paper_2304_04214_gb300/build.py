@@ -32,22 +32,25 @@ def _stale() -> bool:
     return any(os.path.getmtime(f) > t for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the library if missing or older than its sources; return its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, out: str = None, defines=()) -> str:
+    """Compile the library if missing or older than its sources; return its path.
+    out/defines build a variant elsewhere (e.g. another block size)."""
+    if out is None and not force and not _stale():
         return LIB
     nvcc = nvcc_path()
-    tmp = LIB + ".tmp"
+    target = out or LIB
+    tmp = target + ".tmp"
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
            "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC,
+           *[f"-D{d}" for d in defines],
            *[os.path.join(CSRC, s) for s in SOURCES], "-o", tmp]
     if os.environ.get("LBM_PTXAS_VERBOSE"):
         cmd.insert(1, "-Xptxas=-v")
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

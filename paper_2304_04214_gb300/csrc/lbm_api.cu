@@ -60,7 +60,8 @@ struct lbm_handle {
     double delta = 0, utau_ref = 0, nu = 0, tau0 = 0, ubp = 0, maxl = 0;
     // host tables
     std::vector<float> UR, amat, sq, sig;
-    std::vector<uint32_t> alpha, beta, phi32;
+    std::vector<float> sqsig;                 // [ny][N] x (sqrt(6 q), sigma)
+    std::vector<uint32_t> alpha, beta, betaT, phi32;
     std::vector<uint64_t> rate64;
     // device
     bool bound = false, owns = false;
@@ -70,16 +71,19 @@ struct lbm_handle {
     int cur = 0;
     float *d_utau = nullptr, *d_fw = nullptr, *d_uin = nullptr, *d_ubuf = nullptr;
     double *d_st = nullptr, *d_st_utau = nullptr;
-    long long *d_t = nullptr;
     unsigned *d_flags = nullptr;
-    float *d_UR = nullptr, *d_amat = nullptr, *d_sq = nullptr, *d_sig = nullptr;
-    uint32_t *d_alpha = nullptr, *d_beta = nullptr, *d_phi32 = nullptr;
+    float *d_UR = nullptr, *d_amat = nullptr;
+    float4 *d_sqsig = nullptr;
+    uint32_t *d_alpha = nullptr, *d_betaT = nullptr, *d_phi32 = nullptr;
+    // STG ring: inlet velocities of steps [stg_t0, stg_t0 + stg_len)
+    int stg_ring = 1;
+    long long stg_t0 = 0, stg_len = 0;
+    long long check_every = 16;
     uint64_t *d_rate64 = nullptr;
     cudaStream_t stream = nullptr;
     long long t = 0;
     long long steps_since_stats = 0;
     long n_samples = 0;
-    long long t_host_buf = 0;
     // inlet profile (RANS input of Algorithm 1 steps 1-3): U[j], R[6j..6j+5]
     bool custom_profile = false;
     std::vector<double> prof_U, prof_R;
@@ -101,19 +105,19 @@ struct lbm_handle {
         lat[1] = ar.take<char>(19 * (size_t)ncell * elem);
         d_utau = ar.take<float>(2 * (size_t)nz * nx);
         d_fw = ar.take<float>(6 * (size_t)nz * nx);
-        d_uin = ar.take<float>(3 * (size_t)nz * ny);
+        // ring of STG inlet velocities: as many time levels as fit in ~16 MB (<= 64)
+        stg_ring = (int)std::max<size_t>(1, std::min<size_t>(64, (16u << 20) / (12 * (size_t)nz * ny)));
+        d_uin = ar.take<float>(3 * (size_t)nz * ny * stg_ring);
         d_ubuf = opts.stats_every > 0 ? ar.take<float>(3 * (size_t)ncell) : nullptr;
         d_st = ar.take<double>(7 * (size_t)nx * ny);
         d_st_utau = ar.take<double>(2 * (size_t)nx);
-        d_t = ar.take<long long>(1);
         d_tw = ar.take<double>(2 * (size_t)nx);
         d_flags = ar.take<unsigned>(4);
         d_UR = ar.take<float>(ny);
         d_amat = ar.take<float>(6 * (size_t)ny);
-        d_sq = ar.take<float>((size_t)ny * N);
-        d_sig = ar.take<float>(3 * N);
+        d_sqsig = ar.take<float4>((size_t)ny * N);
         d_alpha = ar.take<uint32_t>((size_t)ny * N);
-        d_beta = ar.take<uint32_t>((size_t)nz * N);
+        d_betaT = ar.take<uint32_t>((size_t)nz * N);
         d_phi32 = ar.take<uint32_t>(N);
         d_rate64 = ar.take<uint64_t>(N);
         return (ar.off + 255) & ~size_t(255);
@@ -157,8 +161,9 @@ struct lbm_handle {
         const size_t NN = N > 0 ? N : 1;
         sq.assign((size_t)ny * NN, 0.f);
         sig.assign(3 * NN, 0.f);
+        sqsig.assign(4 * (size_t)ny * NN, 0.f);
         alpha.assign((size_t)ny * NN, 0u);
-        beta.assign((size_t)nz * NN, 0u);
+        betaT.assign((size_t)nz * NN, 0u);
         phi32.assign(NN, 0u);
         rate64.assign(NN, 0ull);
         if (N == 0) { maxl = 0; return; }
@@ -190,8 +195,9 @@ struct lbm_handle {
         }
         for (int j = 0; j < ny; ++j)
             for (int n = 0; n < N; ++n) alpha[(size_t)j * N + n] = turns32(kn[n] * dy[n] * (j + 0.5) / (2 * kPi));
+        betaT.assign((size_t)nz * NN, 0u);
         for (int k = 0; k < nz; ++k)
-            for (int n = 0; n < N; ++n) beta[(size_t)k * N + n] = turns32(kn[n] * dz[n] * (k + 0.5) / (2 * kPi));
+            for (int n = 0; n < N; ++n) betaT[(size_t)n * nz + k] = turns32(kn[n] * dz[n] * (k + 0.5) / (2 * kPi));
         // q_n(y) from the modified von Karman spectrum with Kolmogorov and
         // grid cut-offs; sqrt(6 q_n) stored (the sqrt6 of eq:aux_vec folded in)
         const double kcut = kPi;                        // 2 pi / (2 dx)
@@ -211,6 +217,13 @@ struct lbm_handle {
             }
             for (int n = 0; n < N; ++n) sq[(size_t)j * N + n] = (float)std::sqrt(6.0 * E[n] / tot);
         }
+        sqsig.assign(4 * (size_t)ny * NN, 0.f);
+        for (int j = 0; j < ny; ++j)
+            for (int n = 0; n < N; ++n) {
+                float *e = &sqsig[4 * ((size_t)j * N + n)];
+                e[0] = sq[(size_t)j * N + n];
+                e[1] = sig[n]; e[2] = sig[(size_t)N + n]; e[3] = sig[2 * (size_t)N + n];
+            }
     }
     double opts_kappa0 = 0.4;   // the creation-time kappa (dissipation estimate of the spectrum)
 
@@ -241,10 +254,11 @@ struct lbm_handle {
         const size_t N = n_modes > 0 ? n_modes : 1;
         cudaError_t e;
 #define UP(dst, vec) if ((e = cudaMemcpyAsync(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return e
-        UP(d_UR, UR); UP(d_amat, amat); UP(d_sq, sq); UP(d_sig, sig);
-        UP(d_alpha, alpha); UP(d_beta, beta); UP(d_phi32, phi32); UP(d_rate64, rate64);
+        UP(d_UR, UR); UP(d_amat, amat); UP(d_sqsig, sqsig);
+        UP(d_alpha, alpha); UP(d_betaT, betaT); UP(d_phi32, phi32); UP(d_rate64, rate64);
 #undef UP
         (void)N;
+        stg_len = 0;                            // the STG ring is stale
         return cudaStreamSynchronize(stream);   // host vectors may change after return
     }
 };
@@ -282,22 +296,28 @@ template <class S>
 void launch_step_t(lbm_handle *h, bool stats) {
     using T = typename S::T;
     lbmk::StepArgs<S> a;
-    a.fin = (const T *)h->lat[h->cur];
-    a.fout = (T *)h->lat[h->cur ^ 1];
-    a.uin = h->d_uin;
+    const size_t N = (size_t)h->ncell;
+    for (int q = 0; q < 19; ++q) {
+        a.in[q] = (const T *)h->lat[h->cur] + q * N;
+        a.out[q] = (T *)h->lat[h->cur ^ 1] + q * N;
+    }
+    a.vprime = h->d_uin + 3 * (size_t)h->nz * h->ny * (size_t)(h->t - h->stg_t0);
+    a.UR = h->d_UR;
+    a.amat = h->d_amat;
     a.utau = h->d_utau;
     a.fw = h->d_fw;
     a.ubuf = h->d_ubuf;
     a.flags = h->d_flags;
-    a.t_dev = h->d_t;
-    a.ncell = h->ncell;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
     a.inlet = h->opts.inlet; a.wall_model = h->opts.wall_model;
+    a.check = (h->t % h->check_every) == 0;
+    a.reverse = (int)(h->t & 1);
     a.tau0 = (float)h->tau0;
     a.csm18 = (float)(18.0 * std::sqrt(2.0) * h->opts.c_smag);
     a.y1_nu = (float)(0.5 / h->nu);
     a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
-    const int bx = h->nx >= 64 ? 64 : 32;
+    const int bxmax = lbmk::STEP_THREADS / lbmk::BY;
+    const int bx = h->nx >= bxmax ? bxmax : (h->nx >= 64 && bxmax >= 64 ? 64 : 32);
     dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
     const size_t slot = h->prof_on ? prof_slot(h) : 0;
     if (h->prof_on) cudaEventRecord(h->ev0[slot], h->stream);
@@ -307,15 +327,15 @@ void launch_step_t(lbm_handle *h, bool stats) {
     h->launches += 1;
 }
 
-void launch_stg(lbm_handle *h, const long long *t_dev, long long t_val) {
+// STG inlet velocities of steps t0 .. t0 + n - 1 into the ring slots 0 .. n-1.
+void launch_stg(lbm_handle *h, long long t0, int n, bool apply_profile) {
     lbmk::StgArgs a;
-    a.alpha = h->d_alpha; a.beta = h->d_beta; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
-    a.sq = h->d_sq; a.sig = h->d_sig; a.amat = h->d_amat; a.UR = h->d_UR; a.uin = h->d_uin;
-    a.t_dev = t_dev; a.t_val = t_val;
+    a.alpha = h->d_alpha; a.betaT = h->d_betaT; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
+    a.sqsig = h->d_sqsig; a.amat = h->d_amat; a.UR = h->d_UR; a.out = h->d_uin;
+    a.t0 = t0; a.nsteps = n; a.apply_profile = apply_profile ? 1 : 0;
     a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
-    const int cells = h->ny * h->nz;
-    const int blocks = (cells * 32 + 255) / 256;
-    lbmk::stg_kernel<<<blocks, 256, 0, h->stream>>>(a);
+    dim3 grid((h->nz + lbmk::STG_KZ - 1) / lbmk::STG_KZ, h->ny, (n + lbmk::STG_KT - 1) / lbmk::STG_KT);
+    lbmk::stg_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, h->stream>>>(a);
     h->launches += 1;
 }
 
@@ -325,7 +345,11 @@ int one_step(lbm_handle *h) {
         h->steps_since_stats += 1;
         if (h->steps_since_stats >= h->opts.stats_every) { stats = true; h->steps_since_stats = 0; }
     }
-    if (h->opts.inlet) launch_stg(h, h->d_t, 0);
+    if (h->opts.inlet && (h->t < h->stg_t0 || h->t >= h->stg_t0 + h->stg_len)) {
+        h->stg_t0 = h->t;
+        h->stg_len = h->stg_ring;
+        launch_stg(h, h->stg_t0, h->stg_ring, false);
+    }
     switch (h->opts.precision) {
         case LBM_FP16_DEV: launch_step_t<lbmk::StoreF16>(h, stats); break;
         case LBM_BF16_DEV: launch_step_t<lbmk::StoreBF16>(h, stats); break;
@@ -333,8 +357,10 @@ int one_step(lbm_handle *h) {
     }
     if (stats) {
         h->n_samples += 1;
-        const int n = h->nx * h->ny + 2 * h->nx;
-        lbmk::stats_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(
+        const int cols = (h->nx * h->ny + lbmk::ST_COLS - 1) / lbmk::ST_COLS;
+        const int tb = lbmk::ST_COLS * lbmk::ST_CHUNKS;
+        const int blocks = cols + (h->opts.wall_model ? (2 * h->nx + tb - 1) / tb : 0);
+        lbmk::stats_kernel<<<blocks, tb, 0, h->stream>>>(
             h->d_ubuf, h->d_utau, h->d_st, h->d_st_utau, h->nx, h->ny, h->nz, h->ncell, h->opts.wall_model);
         h->launches += 1;
     }
@@ -616,13 +642,8 @@ int lbm_get_time(const lbm_handle *h, long *t) {
 
 int lbm_set_time(lbm_handle *h, long t) {
     if (!h || t < 0) return LBM_EINVAL;
-    if (!h->bound) return LBM_ESTATE;
     h->t = t;
-    h->t_host_buf = t;
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(h->d_t, &h->t_host_buf, sizeof(long long), cudaMemcpyHostToDevice, h->stream)) !=
-        cudaSuccess) return cuda_fail(e);
-    return cuda_fail(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
 }
 
 int lbm_get_constants(const lbm_handle *h, double out[6]) {
@@ -634,7 +655,8 @@ int lbm_get_constants(const lbm_handle *h, double out[6]) {
 int lbm_inlet_velocity(lbm_handle *h, long t, double *out) {
     if (!h || !out || t < 0) return LBM_EINVAL;
     if (!h->bound) return LBM_ESTATE;
-    launch_stg(h, nullptr, t);
+    launch_stg(h, t, 1, true);
+    h->stg_len = 0;
     cudaError_t e;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     const size_t n = 3 * (size_t)h->ny * h->nz;

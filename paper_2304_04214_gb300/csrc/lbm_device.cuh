@@ -41,24 +41,41 @@ constexpr float S_PI = 1.6f;     // moments 10, 12
 constexpr float S_M = 1.98f;     // moments 16, 17, 18
 
 // ---------------------------------------------------------------------------
-// Storage of one population: registers always hold the shifted value
-// ft = f - w_q in FP32.
+// Storage of one population.  FP32 storage holds f itself; the 16-bit formats
+// hold the deviation f - w_q.  SHIFTED tells the collision which of the two
+// its registers hold (the arithmetic is FP32 either way).
 // ---------------------------------------------------------------------------
 struct StoreF32 {
     using T = float;
-    static __device__ __forceinline__ float ld(const float *p, float w) { return *p - w; }
-    static __device__ __forceinline__ void st(float *p, float v, float w) { *p = v + w; }
+    static constexpr bool SHIFTED = false;
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 struct StoreF16 {
     using T = __half;
-    static __device__ __forceinline__ float ld(const __half *p, float) { return __half2float(*p); }
-    static __device__ __forceinline__ void st(__half *p, float v, float) { *p = __float2half_rn(v); }
+    static constexpr bool SHIFTED = true;
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float) { return __bfloat162float(*p); }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16_rn(v); }
+    static constexpr bool SHIFTED = true;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
+
+// Approximate reciprocal and square root (PTX rcp/sqrt.approx, about one ulp);
+// the collision uses them where a rounding error of that size is harmless.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // ---------------------------------------------------------------------------
 // Reichardt law, Sec. 2.3 eq:reichard with the textbook coefficients
@@ -83,7 +100,7 @@ __device__ __forceinline__ double reichardt_dy_d(double yp, double kap, double B
 
 // Newton solve of eq:u_tau_implicit, u u+(y1 u / nu) = uhat, uhat > 0, warm
 // started; FP32 first, FP64 if FP32 did not settle.  *ok = false if neither did.
-__device__ __noinline__ float solve_utau_dev(float uhat, float y1_nu, float kap, float B, float guess,
+__device__ __forceinline__ float solve_utau_dev(float uhat, float y1_nu, float kap, float B, float guess,
                                              bool *ok) {
     float u = guess > 0.0f ? guess : 1e-3f;
     for (int it = 0; it < 12; ++it) {
@@ -111,59 +128,79 @@ __device__ __noinline__ float solve_utau_dev(float uhat, float y1_nu, float kap,
     return (float)ud;
 }
 
+
 // ---------------------------------------------------------------------------
 // MRT collision with the Guo force in moment space (eq:lbe_mrt,
 // eq:bodyforce; reading: F_force = M^-1 (I - S/2) M F~), Smagorinsky tau_eff
 // (eq:tau_eff) on the viscous moments 9, 11, 13, 14, 15.
 //
-// f[] holds shifted populations f - w.  In: drho = rho - 1, momentum jx..jz
-// (= sum f c), force density F.  The update is f* = f - M^T g with
-// g_k = (s_k (m_k - m_k^eq) - (1 - s_k/2) (M F~)_k) / |row_k|^2, evaluated with
-// sums s_p = f_p + f_{18-p} and differences d_p = f_p - f_{18-p} of the nine
-// opposite pairs; the rows of M are the d'Humieres moments.
+// f[] holds f (SHIFTED = false) or f - w (SHIFTED = true).  In: drho =
+// rho - 1, momentum jx..jz (= sum f c), force density F (HAS_FORCE).  The
+// update is f* = f - M^T g with g_k = (s_k (m_k - m_k^eq) - (1 - s_k/2)
+// (M F~)_k) / |row_k|^2, evaluated with sums s_p = f_p + f_{18-p} and
+// differences d_p = f_p - f_{18-p} of the nine opposite pairs; the rows of M
+// are the d'Humieres moments.  M w = (1, -11, 3, 0, ..., 0) supplies the
+// constant terms that differ between f and f - w.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void collide_mrt(float (&f)[19], float drho, float jx, float jy, float jz,
-                                            float Fx, float Fy, float Fz, float tau0, float csm18,
-                                            float &ux_o, float &uy_o, float &uz_o) {
-    const float s0 = f[0] + f[18], d0 = f[0] - f[18];
-    const float s1 = f[1] + f[17], d1 = f[1] - f[17];
-    const float s2 = f[2] + f[16], d2 = f[2] - f[16];
-    const float s3 = f[3] + f[15], d3 = f[3] - f[15];
-    const float s4 = f[4] + f[14], d4 = f[4] - f[14];
-    const float s5 = f[5] + f[13], d5 = f[5] - f[13];
-    const float s6 = f[6] + f[12], d6 = f[6] - f[12];
-    const float s7 = f[7] + f[11], d7 = f[7] - f[11];
-    const float s8 = f[8] + f[10], d8 = f[8] - f[10];
+struct Pairs {
+    float s[9], d[9];      // s_p = f_p + f_{18-p}, d_p = f_p - f_{18-p}, p = 0..8
+    float drho, jx, jy, jz;
+};
+
+// Pair sums and differences, density deviation and momentum (eq:density,
+// eq:momentum without the force) from f (SHIFTED = false) or f - w.
+template <bool SHIFTED>
+__device__ __forceinline__ void make_pairs(const float (&f)[19], Pairs &P) {
+#pragma unroll
+    for (int p = 0; p < 9; ++p) { P.s[p] = f[p] + f[18 - p]; P.d[p] = f[p] - f[18 - p]; }
+    const float *s = P.s, *d = P.d;
+    P.drho = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + (s[8] + f[9])
+           - (SHIFTED ? 0.0f : 1.0f);
+    P.jx = (d[3] - d[1]) + (d[7] - d[5]) - d[8];
+    P.jy = (d[4] - d[0]) - (d[5] + d[7]) - d[6];
+    P.jz = -(d[0] + d[4]) - (d[1] + d[3]) - d[2];
+}
+
+template <bool SHIFTED, bool HAS_FORCE>
+__device__ __forceinline__ void collide_mrt(float (&f)[19], const Pairs &P, float Fx, float Fy, float Fz,
+                                            float tau0, float csm18, float &ux_o, float &uy_o, float &uz_o) {
+    const float s0 = P.s[0], d0 = P.d[0], s1 = P.s[1], d1 = P.d[1], s2 = P.s[2], d2 = P.d[2];
+    const float s3 = P.s[3], d3 = P.d[3], s4 = P.s[4], d4 = P.d[4], s5 = P.s[5], d5 = P.d[5];
+    const float s6 = P.s[6], d6 = P.d[6], s7 = P.s[7], d7 = P.d[7], s8 = P.s[8], d8 = P.d[8];
     const float f9 = f[9];
+    const float drho = P.drho, jx = P.jx, jy = P.jy, jz = P.jz;
 
     const float rho = 1.0f + drho;
-    const float irho = 1.0f / rho;
+    const float irho = rcp_approx(rho);
     // eq:momentum: rho u = sum f c + F/2
-    const float rux = jx + 0.5f * Fx, ruy = jy + 0.5f * Fy, ruz = jz + 0.5f * Fz;
+    const float rux = HAS_FORCE ? jx + 0.5f * Fx : jx;
+    const float ruy = HAS_FORCE ? jy + 0.5f * Fy : jy;
+    const float ruz = HAS_FORCE ? jz + 0.5f * Fz : jz;
     const float ux = rux * irho, uy = ruy * irho, uz = ruz * irho;
     ux_o = ux; uy_o = uy; uz_o = uz;
     const float uxx = rux * ux, uyy = ruy * uy, uzz = ruz * uz;       // rho u_a u_a
     const float uxy = rux * uy, uyz = ruy * uz, uxz = rux * uz;
     const float usq = uxx + uyy + uzz;
 
-    // non-equilibrium moments n_k = m_k - m_k^eq (m of f, shifted: M w = (1,-11,3,0...))
+    // non-equilibrium moments n_k = m_k - m_k^eq
     const float Sax = s2 + s6 + s8;
     const float Sdg = (s0 + s4) + (s1 + s3) + (s5 + s7);
-    const float n1 = -30.0f * f9 - 11.0f * Sax + 8.0f * Sdg + 11.0f * drho - 19.0f * usq;
-    const float n2 = 12.0f * f9 - 4.0f * Sax + Sdg - 3.0f * drho + 5.5f * usq;
-    const float Dx = (d3 - d1) + (d7 - d5);
-    const float Dy = (d4 - d0) - (d5 + d7);
-    const float Dz = -(d0 + d4) - (d1 + d3);
-    const float n4 = Dx + 4.0f * d8 + (2.0f / 3.0f) * rux;   // q_x + 2/3 rho u_x
-    const float n6 = Dy + 4.0f * d6 + (2.0f / 3.0f) * ruy;
-    const float n8 = Dz + 4.0f * d2 + (2.0f / 3.0f) * ruz;
+    const float e1 = -30.0f * f9 - 11.0f * Sax + 8.0f * Sdg;    // M_1 f
+    const float e2 = 12.0f * f9 - 4.0f * Sax + Sdg;             // M_2 f
+    // m1^eq = -11 rho + 19 rho u^2, m2^eq = 3 rho - 11/2 rho u^2 (= M f^eq)
+    const float n1 = SHIFTED ? e1 + 11.0f * drho - 19.0f * usq : e1 + 11.0f * rho - 19.0f * usq;
+    const float n2 = SHIFTED ? e2 - 3.0f * drho + 5.5f * usq : e2 - 3.0f * rho + 5.5f * usq;
+    // q_a = j_a + 5 d_axis: q_x + 2/3 rho u_x etc.
+    const float n4 = jx + 5.0f * d8 + (2.0f / 3.0f) * rux;
+    const float n6 = jy + 5.0f * d6 + (2.0f / 3.0f) * ruy;
+    const float n8 = jz + 5.0f * d2 + (2.0f / 3.0f) * ruz;
     const float s04 = s0 + s4, s13 = s1 + s3, s57 = s5 + s7;
     const float pxx_eq = 2.0f * uxx - uyy - uzz;                   // m9^eq
     const float pww_eq = uyy - uzz;                                // m11^eq
-    const float n9 = 2.0f * s8 - s2 - s6 - 2.0f * s04 + s13 + s57 - pxx_eq;
-    const float n10 = -4.0f * s8 + 2.0f * (s2 + s6) - 2.0f * s04 + s13 + s57 + 0.5f * pxx_eq;
-    const float n11 = (s6 - s2) + s57 - s13 - pww_eq;
-    const float n12 = 2.0f * (s2 - s6) + s57 - s13 + 0.5f * pww_eq;
+    const float n9 = 2.0f * s8 - (s2 + s6) - 2.0f * s04 + (s13 + s57) - pxx_eq;
+    const float n10 = -4.0f * s8 + 2.0f * (s2 + s6) - 2.0f * s04 + (s13 + s57) + 0.5f * pxx_eq;
+    const float n11 = (s6 - s2) + (s57 - s13) - pww_eq;
+    const float n12 = 2.0f * (s2 - s6) + (s57 - s13) + 0.5f * pww_eq;
     const float n13 = (s5 - s7) - uxy;
     const float n14 = (s0 - s4) - uyz;
     const float n15 = (s1 - s3) - uxz;
@@ -177,210 +214,250 @@ __device__ __forceinline__ void collide_mrt(float (&f)[19], float drho, float jx
     const float pyy = (c2 - 0.5f * n9 + 1.5f * n11) * (1.0f / 3.0f);
     const float pzz = (c2 - 0.5f * n9 - 1.5f * n11) * (1.0f / 3.0f);
     const float qq = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (n13 * n13 + n14 * n14 + n15 * n15);
-    // eq:tau_eff: tau_eff = (tau0 + sqrt(tau0^2 + 18 sqrt2 C Q^(1/2) / rho)) / 2
-    const float te = 0.5f * (tau0 + sqrtf(tau0 * tau0 + csm18 * sqrtf(qq) * irho));
-    const float sv = 1.0f / te;
+    // eq:tau_eff: s_nu = 1 / tau_eff = 2 / (tau0 + sqrt(tau0^2 + 18 sqrt2 C Q^(1/2) / rho))
+    const float sv = 2.0f * rcp_approx(tau0 + sqrt_approx(fmaf(csm18 * sqrt_approx(qq), irho, tau0 * tau0)));
 
-    // moments of the Guo source M F~ (second-order Hermite form)
-    const float uF = ux * Fx + uy * Fy + uz * Fz;
-    const float F9 = 4.0f * ux * Fx - 2.0f * (uy * Fy + uz * Fz);
-    const float F11 = 2.0f * (uy * Fy - uz * Fz);
-    const float F13 = ux * Fy + uy * Fx, F14 = uy * Fz + uz * Fy, F15 = ux * Fz + uz * Fx;
-
-    const float g1 = (S_E * n1 - (1.0f - 0.5f * S_E) * 38.0f * uF) * (1.0f / 2394.0f);
-    const float g2 = (S_EPS * n2 + (1.0f - 0.5f * S_EPS) * 11.0f * uF) * (1.0f / 252.0f);
-    const float g3 = -0.1f * Fx, g5 = -0.1f * Fy, g7 = -0.1f * Fz;
-    const float cq = (1.0f - 0.5f * S_Q) * (2.0f / 3.0f);
-    const float g4 = (S_Q * n4 + cq * Fx) * (1.0f / 40.0f);
-    const float g6 = (S_Q * n6 + cq * Fy) * (1.0f / 40.0f);
-    const float g8 = (S_Q * n8 + cq * Fz) * (1.0f / 40.0f);
-    const float hv = 1.0f - 0.5f * sv;
-    const float g9 = (sv * n9 - hv * F9) * (1.0f / 36.0f);
-    const float g10 = (S_PI * n10 + (1.0f - 0.5f * S_PI) * 0.5f * F9) * (1.0f / 72.0f);
-    const float g11 = (sv * n11 - hv * F11) * (1.0f / 12.0f);
-    const float g12 = (S_PI * n12 + (1.0f - 0.5f * S_PI) * 0.5f * F11) * (1.0f / 24.0f);
-    const float g13 = (sv * n13 - hv * F13) * 0.25f;
-    const float g14 = (sv * n14 - hv * F14) * 0.25f;
-    const float g15 = (sv * n15 - hv * F15) * 0.25f;
-    const float g16 = S_M * n16 * 0.125f, g17 = S_M * n17 * 0.125f, g18 = S_M * n18 * 0.125f;
+    float G1, G2 = S_EPS * n2 * (1.0f / 252.0f);
+    float G3 = 0.0f, G5 = 0.0f, G7 = 0.0f;
+    float G4 = S_Q * n4 * (1.0f / 40.0f), G6 = S_Q * n6 * (1.0f / 40.0f), G8 = S_Q * n8 * (1.0f / 40.0f);
+    float G9 = sv * n9 * (1.0f / 36.0f), G10 = S_PI * n10 * (1.0f / 72.0f);
+    float G11 = sv * n11 * (1.0f / 12.0f), G12 = S_PI * n12 * (1.0f / 24.0f);
+    float G13 = sv * n13 * 0.25f, G14 = sv * n14 * 0.25f, G15 = sv * n15 * 0.25f;
+    if (HAS_FORCE) {
+        // moments of the Guo source M F~ (second-order Hermite form)
+        const float uF = ux * Fx + uy * Fy + uz * Fz;
+        const float F9 = 4.0f * ux * Fx - 2.0f * (uy * Fy + uz * Fz);
+        const float F11 = 2.0f * (uy * Fy - uz * Fz);
+        const float F13 = ux * Fy + uy * Fx, F14 = uy * Fz + uz * Fy, F15 = ux * Fz + uz * Fx;
+        const float hv = 1.0f - 0.5f * sv;
+        const float cq = (1.0f - 0.5f * S_Q) * (2.0f / 3.0f);
+        G1 = (S_E * n1 - (1.0f - 0.5f * S_E) * 38.0f * uF) * (1.0f / 2394.0f);
+        G2 += (1.0f - 0.5f * S_EPS) * 11.0f * uF * (1.0f / 252.0f);
+        G3 = -0.1f * Fx; G5 = -0.1f * Fy; G7 = -0.1f * Fz;
+        G4 += cq * Fx * (1.0f / 40.0f); G6 += cq * Fy * (1.0f / 40.0f); G8 += cq * Fz * (1.0f / 40.0f);
+        G9 -= hv * F9 * (1.0f / 36.0f);
+        G10 += (1.0f - 0.5f * S_PI) * 0.5f * F9 * (1.0f / 72.0f);
+        G11 -= hv * F11 * (1.0f / 12.0f);
+        G12 += (1.0f - 0.5f * S_PI) * 0.5f * F11 * (1.0f / 24.0f);
+        G13 -= hv * F13 * 0.25f; G14 -= hv * F14 * 0.25f; G15 -= hv * F15 * 0.25f;
+    } else {
+        G1 = S_E * n1 * (1.0f / 2394.0f);
+    }
+    const float G16 = S_M * n16 * 0.125f, G17 = S_M * n17 * 0.125f, G18 = S_M * n18 * 0.125f;
 
     // f* = f - M^T g, by opposite pairs: even part E (same for p and 18-p),
     // odd part O (sign flips).
-    const float Aax = -11.0f * g1 - 4.0f * g2;
-    const float Ddg = 8.0f * g1 + g2;
-    const float Jx = g3 + g4, Jy = g5 + g6, Jz = g7 + g8;
-    const float g9_10 = g9 + g10, g11_12 = g11 + g12;
+    const float Aax = -11.0f * G1 - 4.0f * G2;
+    const float Ddg = 8.0f * G1 + G2;
+    const float Jx = G3 + G4, Jy = G5 + G6, Jz = G7 + G8;
+    const float g9_10 = G9 + G10, g11_12 = G11 + G12;
     float E, O;
-    E = Ddg - 2.0f * g9_10 + g14;              O = -Jy - Jz - g17 + g18;      // pair 0/18
+    E = Ddg - 2.0f * g9_10 + G14;              O = -Jy - Jz - G17 + G18;      // pair 0/18
     f[0] -= E + O; f[18] -= E - O;
-    E = Ddg + g9_10 - g11_12 + g15;            O = -Jx - Jz + g16 - g18;      // pair 1/17
+    E = Ddg + g9_10 - g11_12 + G15;            O = -Jx - Jz + G16 - G18;      // pair 1/17
     f[1] -= E + O; f[17] -= E - O;
-    E = Aax - g9 + 2.0f * g10 - g11 + 2.0f * g12; O = -g7 + 4.0f * g8;        // pair 2/16
+    E = Aax - G9 + 2.0f * G10 - G11 + 2.0f * G12; O = -G7 + 4.0f * G8;        // pair 2/16
     f[2] -= E + O; f[16] -= E - O;
-    E = Ddg + g9_10 - g11_12 - g15;            O = Jx - Jz - g16 - g18;       // pair 3/15
+    E = Ddg + g9_10 - g11_12 - G15;            O = Jx - Jz - G16 - G18;       // pair 3/15
     f[3] -= E + O; f[15] -= E - O;
-    E = Ddg - 2.0f * g9_10 - g14;              O = Jy - Jz + g17 + g18;       // pair 4/14
+    E = Ddg - 2.0f * g9_10 - G14;              O = Jy - Jz + G17 + G18;       // pair 4/14
     f[4] -= E + O; f[14] -= E - O;
-    E = Ddg + g9_10 + g11_12 + g13;            O = -Jx - Jy - g16 + g17;      // pair 5/13
+    E = Ddg + g9_10 + g11_12 + G13;            O = -Jx - Jy - G16 + G17;      // pair 5/13
     f[5] -= E + O; f[13] -= E - O;
-    E = Aax - g9 + 2.0f * g10 + g11 - 2.0f * g12; O = -g5 + 4.0f * g6;        // pair 6/12
+    E = Aax - G9 + 2.0f * G10 + G11 - 2.0f * G12; O = -G5 + 4.0f * G6;        // pair 6/12
     f[6] -= E + O; f[12] -= E - O;
-    E = Ddg + g9_10 + g11_12 - g13;            O = Jx - Jy + g16 + g17;       // pair 7/11
+    E = Ddg + g9_10 + g11_12 - G13;            O = Jx - Jy + G16 + G17;       // pair 7/11
     f[7] -= E + O; f[11] -= E - O;
-    E = Aax + 2.0f * g9 - 4.0f * g10;          O = -g3 + 4.0f * g4;           // pair 8/10
+    E = Aax + 2.0f * G9 - 4.0f * G10;          O = -G3 + 4.0f * G4;           // pair 8/10
     f[8] -= E + O; f[10] -= E - O;
-    f[9] += 30.0f * g1 - 12.0f * g2;
+    f[9] += 30.0f * G1 - 12.0f * G2;
 }
 
 // ---------------------------------------------------------------------------
-// Arguments of the fused step kernel.
+// Pull source of population q for cell (i, j, k) under the boundary rules:
+// z periodic; x clamped (inlet on: the inlet rebuilds c_x > 0, the outlet
+// copy is the clamp at nx-1) or periodic; specular slip walls mirror c_y and
+// read from the same row.  Returns the source plane and the cell offset.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int mirror_y(int q) {
+    // pairs (0,4), (5,11), (6,12), (7,13), (14,18)
+    return (q == 0) ? 4 : (q == 4) ? 0 : (q == 14) ? 18 : (q == 18) ? 14
+         : (q == 5 || q == 6 || q == 7) ? q + 6 : (q == 11 || q == 12 || q == 13) ? q - 6 : q;
+}
+__device__ __forceinline__ void pull_source(int q, int i, int j, int k, int nx, int ny, int nz, int inlet,
+                                            int &plane, int &off) {
+    int sx = i - CX(q), sy = j - CY(q), sz = k - CZ(q);
+    sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
+    if (inlet) sx = min(max(sx, 0), nx - 1);
+    else sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+    plane = q;
+    if (sy < 0 || sy >= ny) { sy = j; plane = mirror_y(q); }
+    off = (sz * ny + sy) * nx + sx;
+}
+
+// ---------------------------------------------------------------------------
+// Arguments of the fused step kernel.  Every population plane has its own
+// base pointer (offsets stay 32-bit).
 // ---------------------------------------------------------------------------
 template <class S>
 struct StepArgs {
-    const typename S::T *__restrict__ fin;   // post-collision state, read by pull
-    typename S::T *__restrict__ fout;        // new post-collision state
-    const float *__restrict__ uin;           // [nz][ny][3] inlet velocity of this step
+    const typename S::T *in[19];             // post-collision state, read by pull
+    typename S::T *out[19];                  // new post-collision state
+    const float *__restrict__ vprime;        // [nz][ny][3] STG field v' of this step (eq:aux_vec)
+    const float *__restrict__ UR;            // [ny] inlet mean profile (eq:u_couple)
+    const float *__restrict__ amat;          // [ny][6] amp * Cholesky factor (eq:v_fluc)
     float *__restrict__ utau;                // [2][nz][nx] wall friction velocity
     float *__restrict__ fw;                  // [2][nz][nx][3] wall force of this step
     float *__restrict__ ubuf;                // [3][ncell] velocity (statistics steps)
     unsigned *__restrict__ flags;            // [0] Newton failures, [1] divergence
-    long long *__restrict__ t_dev;           // STG time, advanced once per step
-    long long ncell;
     int nx, ny, nz;
     int inlet, wall_model;
+    int check;                               // test |u| < 0.3 and finiteness this step
+    int reverse;                             // traverse the lattice backwards this step
     float tau0, csm18;                       // tau0, 18 sqrt2 C_smag
     float y1_nu, kappa, B;                   // y1 / nu, Reichardt constants
 };
 
 constexpr int BY = 2;  // rows per block: (0,1) and (ny-2,ny-1) share a block
+#ifndef LBM_STEP_THREADS
+#define LBM_STEP_THREADS 128   // threads per block of the step kernel (BX x BY)
+#endif
+#ifndef LBM_STEP_MINB
+#define LBM_STEP_MINB 8        // resident blocks per SM the register budget aims for
+#endif
+constexpr int STEP_THREADS = LBM_STEP_THREADS;
 
-// One time step of Algorithm 1 for every cell: pull streaming with the
-// boundary rules, regularized STG inlet at x = 0 (steps 6-8), Reichardt wall
-// force on j = 0 and j = ny-1 (steps 9-14), MRT-LES collision (step 15).
-template <class S, bool STATS>
-__global__ void __launch_bounds__(128) step_kernel(const StepArgs<S> a) {
-    using T = typename S::T;
-    __shared__ float su2[128 / BY][3];
-
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = blockIdx.x * blockDim.x + tx;
-    const int j = blockIdx.y * BY + ty;
-    const int k = blockIdx.z;
-    const bool valid = i < nx;
-    const int ic = valid ? i : nx - 1;
-    const long long N = a.ncell;
-
-    // pull sources: x - c_x with a clamp (inlet / zero-gradient outlet) or wrap
-    int xm = ic - 1, xp = ic + 1;
-    if (a.inlet) { xm = max(xm, 0); xp = min(xp, nx - 1); }
-    else { xm = xm < 0 ? nx - 1 : xm; xp = xp >= nx ? 0 : xp; }
-    const int km = k == 0 ? nz - 1 : k - 1;          // source plane for c_z = +1
-    const int kp = k == nz - 1 ? 0 : k + 1;          // source plane for c_z = -1
-    const bool bot = j == 0, top = j == ny - 1;
-    const int jm = bot ? 0 : j - 1;                  // for c_y = +1 (mirror at the bottom wall)
-    const int jp = top ? j : j + 1;                  // for c_y = -1 (mirror at the top wall)
-    const int rk = k * ny, rkm = km * ny, rkp = kp * ny;
-    // row starts
-    const int r00 = (rk + j) * nx, r0m = (rkm + j) * nx, r0p = (rkp + j) * nx;
-    const int rm0 = (rk + jm) * nx, rmm = (rkm + jm) * nx, rmp = (rkp + jm) * nx;
-    const int rp0 = (rk + jp) * nx, rpm = (rkm + jp) * nx, rpp = (rkp + jp) * nx;
-    // specular slip walls: a population leaving through the wall comes back
-    // with c_y mirrored from the same cell row (mirror pairs 0-4, 5-11, 6-12,
-    // 7-13, 14-18).
-    const long long mt4 = top ? 4 * N : 0, mt6 = top ? 6 * N : 0;
-    const long long mb4 = bot ? -4 * N : 0, mb6 = bot ? -6 * N : 0;
-    const T *fi = a.fin;
-
-    float f[19];
-    f[0] = S::ld(fi + 0 * N + mt4 + rpp + ic, WQ(0));
-    f[1] = S::ld(fi + 1 * N + r0p + xp, WQ(1));
-    f[2] = S::ld(fi + 2 * N + r0p + ic, WQ(2));
-    f[3] = S::ld(fi + 3 * N + r0p + xm, WQ(3));
-    f[4] = S::ld(fi + 4 * N + mb4 + rmp + ic, WQ(4));
-    f[5] = S::ld(fi + 5 * N + mt6 + rp0 + xp, WQ(5));
-    f[6] = S::ld(fi + 6 * N + mt6 + rp0 + ic, WQ(6));
-    f[7] = S::ld(fi + 7 * N + mt6 + rp0 + xm, WQ(7));
-    f[8] = S::ld(fi + 8 * N + r00 + xp, WQ(8));
-    f[9] = S::ld(fi + 9 * N + r00 + ic, WQ(9));
-    f[10] = S::ld(fi + 10 * N + r00 + xm, WQ(10));
-    f[11] = S::ld(fi + 11 * N + mb6 + rm0 + xp, WQ(11));
-    f[12] = S::ld(fi + 12 * N + mb6 + rm0 + ic, WQ(12));
-    f[13] = S::ld(fi + 13 * N + mb6 + rm0 + xm, WQ(13));
-    f[14] = S::ld(fi + 14 * N + mt4 + rpm + ic, WQ(14));
-    f[15] = S::ld(fi + 15 * N + r0m + xp, WQ(15));
-    f[16] = S::ld(fi + 16 * N + r0m + ic, WQ(16));
-    f[17] = S::ld(fi + 17 * N + r0m + xm, WQ(17));
-    f[18] = S::ld(fi + 18 * N + mb4 + rmm + ic, WQ(18));
-
-    // ---- regularized velocity inlet (Sec. 3.1), lane with i = 0 only ----
-    if (a.inlet && i == 0) {
-        const float *up = a.uin + ((size_t)k * ny + j) * 3;
-        const float vx = up[0], vy = up[1], vz = up[2];
-        // Zou-He density from the known populations (c_x <= 0)
-        const float sk = (f[0] + f[2] + f[4] + f[6] + f[9] + f[12] + f[14] + f[16] + f[18])
-                       + 2.0f * (f[1] + f[5] + f[8] + f[11] + f[15]);
-        const float rin = (1.0f + sk) / (1.0f - vx);
-        const float drin = rin - 1.0f;
-        const float vv = vx * vx + vy * vy + vz * vz;
-        float feq[19], fneq[19];
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
-            feq[q] = WQ(q) * (drin + rin * (3.0f * cu + 4.5f * cu * cu - 1.5f * vv));
-        }
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            // unknown populations (c_x > 0) take f^neq of the opposite direction
-            fneq[q] = CX(q) > 0 ? (f[18 - q] - feq[18 - q]) : (f[q] - feq[q]);
-        }
-        float pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0, tr = 0;
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            pxx += CX(q) * CX(q) * fneq[q]; pyy += CY(q) * CY(q) * fneq[q]; pzz += CZ(q) * CZ(q) * fneq[q];
-            pxy += CX(q) * CY(q) * fneq[q]; pyz += CY(q) * CZ(q) * fneq[q]; pxz += CX(q) * CZ(q) * fneq[q];
-            tr += fneq[q];
-        }
-        // Pi_neq = sum_q Q_q f^neq_q, Q_q = c c - I/3
-        pxx -= tr * (1.0f / 3.0f); pyy -= tr * (1.0f / 3.0f); pzz -= tr * (1.0f / 3.0f);
-        const float trp = (pxx + pyy + pzz) * (1.0f / 3.0f);
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const float qp = CX(q) * CX(q) * pxx + CY(q) * CY(q) * pyy + CZ(q) * CZ(q) * pzz
-                           + 2.0f * (CX(q) * CY(q) * pxy + CY(q) * CZ(q) * pyz + CX(q) * CZ(q) * pxz) - trp;
-            f[q] = feq[q] + 4.5f * WQ(q) * qp;   // w / (2 cs^4) = 9 w / 2
-        }
+// Load the 19 pulled populations.  WALL: the row touches a slip wall, so the
+// populations that would come through it are read mirrored from this row.
+template <class S, bool WALL>
+__device__ __forceinline__ void load_pulled(const StepArgs<S> &a, float (&f)[19], int o00, int ozm, int ozp,
+                                            int oym, int oyp, int ic, int xm, int xp, bool bot, bool top) {
+    // source offsets: row shift -c_y, plane shift -c_z (ozm: source for c_z=+1)
+    const int rm = o00 + oym, rp = o00 + oyp;      // rows for c_y = +1 / -1
+#define LDQ(q, plane, off) f[q] = S::ld(a.in[plane] + (off))
+    LDQ(1, 1, o00 + ozp + xp);  LDQ(2, 2, o00 + ozp + ic);  LDQ(3, 3, o00 + ozp + xm);
+    LDQ(8, 8, o00 + xp);        LDQ(9, 9, o00 + ic);        LDQ(10, 10, o00 + xm);
+    LDQ(15, 15, o00 + ozm + xp); LDQ(16, 16, o00 + ozm + ic); LDQ(17, 17, o00 + ozm + xm);
+    if (!WALL) {
+        LDQ(0, 0, rp + ozp + ic);   LDQ(4, 4, rm + ozp + ic);
+        LDQ(5, 5, rp + xp);         LDQ(6, 6, rp + ic);         LDQ(7, 7, rp + xm);
+        LDQ(11, 11, rm + xp);       LDQ(12, 12, rm + ic);       LDQ(13, 13, rm + xm);
+        LDQ(14, 14, rp + ozm + ic); LDQ(18, 18, rm + ozm + ic);
+    } else {
+        // c_y = -1 populations (0, 5, 6, 7, 14) come from row j+1, or at the top
+        // wall from this row with c_y mirrored (4, 11, 12, 13, 18); and the other way
+        // round for c_y = +1 at the bottom wall.
+        LDQ(0, top ? 4 : 0, rp + ozp + ic);      LDQ(4, bot ? 0 : 4, rm + ozp + ic);
+        LDQ(5, top ? 11 : 5, rp + xp);           LDQ(6, top ? 12 : 6, rp + ic);
+        LDQ(7, top ? 13 : 7, rp + xm);           LDQ(11, bot ? 5 : 11, rm + xp);
+        LDQ(12, bot ? 6 : 12, rm + ic);          LDQ(13, bot ? 7 : 13, rm + xm);
+        LDQ(14, top ? 18 : 14, rp + ozm + ic);   LDQ(18, bot ? 14 : 18, rm + ozm + ic);
     }
+#undef LDQ
+}
 
-    // ---- macroscopic moments (eq:density, eq:momentum without the force) ----
-    float drho = 0.0f;
+// Regularized velocity inlet (Sec. 3.1, Algorithm 1 steps 6-7) for the cell at
+// x = 0: rebuild all 19 populations from the known ones (c_x <= 0) and
+// u_in = (U_R, 0, 0) + a v' (eq:u_couple, eq:v_fluc).
+template <class S>
+__device__ __forceinline__ void inlet_rebuild(const StepArgs<S> &a, float (&f)[19], int j, int k) {
+    const int ny = a.ny;
+    const float *vp = a.vprime + ((size_t)k * ny + j) * 3;
+    const float *m = a.amat + 6 * j;
+    const float vx = a.UR[j] + m[0] * vp[0];
+    const float vy = m[1] * vp[0] + m[2] * vp[1];
+    const float vz = m[3] * vp[0] + m[4] * vp[1] + m[5] * vp[2];
+    if (!S::SHIFTED) {
 #pragma unroll
-    for (int q = 0; q < 19; ++q) drho += f[q];
-    const float jx = (f[3] + f[7] + f[10] + f[13] + f[17]) - (f[1] + f[5] + f[8] + f[11] + f[15]);
-    const float jy = (f[4] + f[11] + f[12] + f[13] + f[18]) - (f[0] + f[5] + f[6] + f[7] + f[14]);
-    const float jz = (f[14] + f[15] + f[16] + f[17] + f[18]) - (f[0] + f[1] + f[2] + f[3] + f[4]);
+        for (int q = 0; q < 19; ++q) f[q] -= WQ(q);
+    }
+    // Zou-He density from the known populations; with f - w the weights
+    // contribute exactly 1
+    const float sk = (f[0] + f[2] + f[4] + f[6] + f[9] + f[12] + f[14] + f[16] + f[18])
+                   + 2.0f * (f[1] + f[5] + f[8] + f[11] + f[15]);
+    const float rin = (1.0f + sk) / (1.0f - vx);
+    const float drin = rin - 1.0f;
+    const float vv = vx * vx + vy * vy + vz * vz;
+    // f^eq_q - w_q of eq:bc_eq at (rho_in, u_in)
+    auto feq = [&](int q) {
+        const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
+        return WQ(q) * (drin + rin * (3.0f * cu + 4.5f * cu * cu - 1.5f * vv));
+    };
+    // f^neq in place: known populations (c_x <= 0) first, then the unknown
+    // ones (c_x > 0) take f^neq of the opposite direction
+#pragma unroll
+    for (int q = 0; q < 19; ++q) if (CX(q) <= 0) f[q] -= feq(q);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) if (CX(q) > 0) f[q] = f[18 - q];
+    float pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0, tr = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        pxx += CX(q) * CX(q) * f[q]; pyy += CY(q) * CY(q) * f[q]; pzz += CZ(q) * CZ(q) * f[q];
+        pxy += CX(q) * CY(q) * f[q]; pyz += CY(q) * CZ(q) * f[q]; pxz += CX(q) * CZ(q) * f[q];
+        tr += f[q];
+    }
+    // Pi_neq = sum_q Q_q f^neq_q with Q_q = c c - I/3
+    pxx -= tr * (1.0f / 3.0f); pyy -= tr * (1.0f / 3.0f); pzz -= tr * (1.0f / 3.0f);
+    const float trp = (pxx + pyy + pzz) * (1.0f / 3.0f);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const float qp = CX(q) * CX(q) * pxx + CY(q) * CY(q) * pyy + CZ(q) * CZ(q) * pzz
+                       + 2.0f * (CX(q) * CY(q) * pxy + CY(q) * CZ(q) * pyz + CX(q) * CZ(q) * pxz) - trp;
+        f[q] = feq(q) + 4.5f * WQ(q) * qp + (S::SHIFTED ? 0.0f : WQ(q));   // w / (2 cs^4) = 9 w / 2
+    }
+}
 
-    // ---- wall model (Sec. 2.3) on the first off-wall cells ----
+// Store the post-collision populations and the statistics / divergence checks.
+template <class S, bool STATS>
+__device__ __forceinline__ void finish_cell(const StepArgs<S> &a, const float (&f)[19], int c, float ux, float uy,
+                                            float uz) {
+#pragma unroll
+    for (int q = 0; q < 19; ++q) S::st(a.out[q] + c, f[q]);
+    if (STATS) {
+        const long long N = (long long)a.nx * a.ny * a.nz;
+        a.ubuf[c] = ux; a.ubuf[N + c] = uy; a.ubuf[2 * N + c] = uz;
+    }
+    if (a.check) {
+        const float uu = ux * ux + uy * uy + uz * uz;
+        if (!(uu < 0.09f)) atomicAdd(a.flags + 1, 1u);    // also catches NaN
+    }
+}
+
+// The first and last block rows: the cells next to the slip walls (mirrored
+// pulls) and the wall model (Sec. 2.3, Algorithm 1 steps 9-14) on the first
+// off-wall cells, whose second cell sits in the same block.  Kept out of line
+// so that the interior path gets its own register allocation.
+template <class S, bool STATS>
+__device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k, int tx, int o00, int ozm,
+                                       int ozp, int ic, int xm, int xp) {
+    __shared__ float su2[STEP_THREADS / BY][3];
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const bool bot = j == 0, top = j == ny - 1;
+    const bool valid = i < nx;
+    const int oym = bot ? 0 : -nx, oyp = top ? 0 : nx;
+    float f[19];
+    if (bot || top) load_pulled<S, true>(a, f, o00, ozm, ozp, oym, oyp, ic, xm, xp, bot, top);
+    else load_pulled<S, false>(a, f, o00, ozm, ozp, oym, oyp, ic, xm, xp, bot, top);
+    if (a.inlet && i == 0) inlet_rebuild<S>(a, f, j, k);
+    Pairs P;
+    make_pairs<S::SHIFTED>(f, P);
+    float ux, uy, uz;
     float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
-    const bool wall_block = a.wall_model && (blockIdx.y == 0 || blockIdx.y == gridDim.y - 1);
-    if (wall_block) {                                   // block-uniform
-        const bool is_wall = bot || top;
-        const float irho = 1.0f / (1.0f + drho);
-        if (!is_wall) { su2[tx][0] = jx * irho; su2[tx][1] = jy * irho; su2[tx][2] = jz * irho; }
+    const bool is_wall = bot || top;
+    if (a.wall_model) {                                   // block-uniform
+        const float irho = 1.0f / (1.0f + P.drho);
+        if (!is_wall) { su2[tx][0] = P.jx * irho; su2[tx][1] = P.jy * irho; su2[tx][2] = P.jz * irho; }
         __syncthreads();
         if (is_wall && valid) {
             const int w = bot ? 0 : 1;
-            const float ny_ = bot ? 1.0f : -1.0f;      // wall normal into the fluid
-            const float u2x = su2[tx][0], u2y = su2[tx][1], u2z = su2[tx][2];
-            // eq:base: tangential part of u_2, normalized
-            const float un = u2y * ny_;
-            const float tx_ = u2x, ty_ = u2y - un * ny_, tz_ = u2z;
-            const float tn = sqrtf(tx_ * tx_ + ty_ * ty_ + tz_ * tz_);
+            const float u2x = su2[tx][0], u2z = su2[tx][2];
+            // eq:base: tangential part of u_2 (the wall normal is along y), normalized
+            const float tn = sqrtf(u2x * u2x + u2z * u2z);
             float *utp = a.utau + ((size_t)w * nz + k) * nx + i;
             if (tn >= 1e-12f) {
-                const float ex = tx_ / tn, ey = ty_ / tn, ez = tz_ / tn;
+                const float ex = u2x / tn, ez = u2z / tn;
                 // eq:uhat with the first-cell velocity (no half-force term)
-                const float uhat = (jx * ex + jy * ey + jz * ez) * irho;
+                const float uhat = (P.jx * ex + P.jz * ez) * irho;
                 const float sg = uhat < 0.0f ? -1.0f : 1.0f;
                 const float ua = fabsf(uhat);
                 float ut = 0.0f;
@@ -391,86 +468,124 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs<S> a) {
                 }
                 *utp = ut;
                 // tau_w = rho u_tau^2, eq:force_wm with A = 1
-                const float tw = (1.0f + drho) * ut * ut * sg;
-                Fx = -tw * ex; Fy = -tw * ey; Fz = -tw * ez;
+                const float tw = (1.0f + P.drho) * ut * ut * sg;
+                Fx = -tw * ex; Fz = -tw * ez;
             }
             float *fwp = a.fw + (((size_t)w * nz + k) * nx + i) * 3;
             fwp[0] = Fx; fwp[1] = Fy; fwp[2] = Fz;
         }
     }
+    if (a.wall_model && is_wall) collide_mrt<S::SHIFTED, true>(f, P, Fx, Fy, Fz, a.tau0, a.csm18, ux, uy, uz);
+    else collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, a.tau0, a.csm18, ux, uy, uz);
+    if (valid) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
+}
 
-    float ux, uy, uz;
-    collide_mrt(f, drho, jx, jy, jz, Fx, Fy, Fz, a.tau0, a.csm18, ux, uy, uz);
+// One time step of Algorithm 1 for every cell: pull streaming with the
+// boundary rules, the regularized inlet at x = 0 (steps 6-8), the Reichardt
+// wall force on j = 0 and j = ny-1 (steps 9-14), the MRT-LES collision (step 15).
+template <class S, bool STATS>
+__global__ void __launch_bounds__(LBM_STEP_THREADS, LBM_STEP_MINB) step_kernel(const __grid_constant__ StepArgs<S> a) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // every other step runs the blocks in reverse order, so that a step starts
+    // on the planes the previous step wrote last (still resident in L2)
+    const int bxi = a.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int byi = a.reverse ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+    const int i = bxi * blockDim.x + tx;
+    const int j = byi * BY + ty;
+    const int k = a.reverse ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    const int ic = i < nx ? i : nx - 1;
 
-    if (!valid) return;
-    const long long c = r00 + i;
-    T *fo = a.fout;
-#pragma unroll
-    for (int q = 0; q < 19; ++q) S::st(fo + q * N + c, f[q], WQ(q));
+    int xm = ic - 1, xp = ic + 1;                    // sources for c_x = +1 / -1
+    if (a.inlet) { xm = max(xm, 0); xp = min(xp, nx - 1); }
+    else { xm = xm < 0 ? nx - 1 : xm; xp = xp >= nx ? 0 : xp; }
+    const int plane = nx * ny;
+    const int ozm = k == 0 ? (nz - 1) * plane : -plane;     // source plane for c_z = +1
+    const int ozp = k == nz - 1 ? -(nz - 1) * plane : plane;  // source plane for c_z = -1
+    const int o00 = (k * ny + j) * nx;
 
-    if (STATS) {
-        a.ubuf[c] = ux; a.ubuf[N + c] = uy; a.ubuf[2 * N + c] = uz;
+    if (byi == 0 || byi == gridDim.y - 1) {               // block-uniform
+        wall_rows<S, STATS>(a, i, j, k, tx, o00, ozm, ozp, ic, xm, xp);
+        return;
     }
-    const float uu = ux * ux + uy * uy + uz * uz;
-    if (!(uu < 0.09f)) atomicAdd(a.flags + 1, 1u);        // also catches NaN
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tx == 0 && ty == 0) *a.t_dev += 1;
+    float f[19];
+    load_pulled<S, false>(a, f, o00, ozm, ozp, -nx, nx, ic, xm, xp, false, false);
+    if (a.inlet && i == 0) inlet_rebuild<S>(a, f, j, k);
+    Pairs P;
+    make_pairs<S::SHIFTED>(f, P);
+    float ux, uy, uz;
+    collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, a.tau0, a.csm18, ux, uy, uz);
+    if (i < nx) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
 }
 
 // ---------------------------------------------------------------------------
-// STG inlet velocity (Sec. 3.1 eq:u_couple, eq:v_fluc, eq:aux_vec).  One warp
-// per inlet cell; lanes split the N modes and reduce by warp shuffles.  The
-// phase k_n d_n . x' + phi_n is carried in 32-bit fixed-point turns:
-//   alpha[j][n] = k_n d_ny y_j / 2pi,  beta[k][n] = k_n d_nz z_k / 2pi,
-//   phi32[n] = phi_n / 2pi,  time part -nu_n t with nu_n = d_nx U_b / max l_e
+// STG field v' for a batch of steps (Sec. 3.1 eq:aux_vec, Algorithm 1 step 4).
+// It depends neither on the flow nor on the inlet profile, so one launch fills
+// a ring of nsteps time levels; the step kernel applies u_in = U_R + a v'.  Block = one row j, 32 spanwise
+// cells x 8 time levels; the mode tables of the row sit in shared memory.
+// The phase k_n d_n . x' + phi_n is carried in 32-bit fixed-point turns:
+//   alpha[j][n] = k_n d_ny y_j / 2pi, beta[k][n] = k_n d_nz z_k / 2pi,
+//   phi32[n] = phi_n / 2pi, and the time part -nu_n t (nu_n = d_nx U_b / max l_e)
 // in 64-bit fixed point, so the argument stays exact for any t.
 // ---------------------------------------------------------------------------
 struct StgArgs {
     const uint32_t *__restrict__ alpha;   // [ny][N]
-    const uint32_t *__restrict__ beta;    // [nz][N]
+    const uint32_t *__restrict__ betaT;   // [N][nz]
     const uint32_t *__restrict__ phi32;   // [N]
     const uint64_t *__restrict__ rate64;  // [N]  (-nu_n) in 2^-64 turns per step
-    const float *__restrict__ sq;         // [ny][N] sqrt(6 q_n(y))
-    const float *__restrict__ sig;        // [3][N] sigma_n
+    const float4 *__restrict__ sqsig;     // [ny][N] (sqrt(6 q_n(y)), sigma_n)
     const float *__restrict__ amat;       // [ny][6] amp * Cholesky factor
     const float *__restrict__ UR;         // [ny] mean profile
-    float *__restrict__ uin;              // [nz][ny][3]
-    const long long *__restrict__ t_dev;  // time (if not null) ...
-    long long t_val;                      // ... else this time
-    int ny, nz, n_modes;
+    float *__restrict__ out;              // [nsteps][nz][ny][3]: v', or u_in if apply_profile
+    long long t0;                         // time of slot 0
+    int nsteps, ny, nz, n_modes;
+    int apply_profile;
 };
 
-__global__ void __launch_bounds__(256) stg_kernel(const StgArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (cell >= a.ny * a.nz) return;                  // whole warp
-    const int j = cell % a.ny, k = cell / a.ny;
+constexpr int STG_KZ = 32, STG_KT = 8, STG_MCHUNK = 256;
+
+__global__ void __launch_bounds__(STG_KZ * STG_KT) stg_kernel(const __grid_constant__ StgArgs a) {
+    __shared__ uint32_t s_ph[STG_KT][STG_MCHUNK];   // alpha + phi + time part, per time level
+    __shared__ float4 s_sq[STG_MCHUNK];
+    const int j = blockIdx.y;
+    const int lz = threadIdx.x % STG_KZ, lt = threadIdx.x / STG_KZ;
+    const int k = blockIdx.x * STG_KZ + lz;
+    const int ts = blockIdx.z * STG_KT + lt;
     const int N = a.n_modes;
-    const uint64_t t = (uint64_t)(a.t_dev ? *a.t_dev : a.t_val);
-    const uint32_t *al = a.alpha + (size_t)j * N;
-    const uint32_t *be = a.beta + (size_t)k * N;
-    const float *sq = a.sq + (size_t)j * N;
     float vx = 0.0f, vy = 0.0f, vz = 0.0f;
-    for (int n = lane; n < N; n += 32) {
-        const uint32_t tt = (uint32_t)((a.rate64[n] * t) >> 32);
-        const uint32_t ph = al[n] + be[n] + a.phi32[n] + tt;
-        const float x = (float)(int32_t)ph * 1.4629180792671596e-09f;   // 2 pi / 2^32
-        const float cw = sq[n] * __cosf(x);
-        vx = fmaf(cw, a.sig[n], vx);
-        vy = fmaf(cw, a.sig[N + n], vy);
-        vz = fmaf(cw, a.sig[2 * N + n], vz);
+    for (int n0 = 0; n0 < N; n0 += STG_MCHUNK) {
+        const int nc = min(STG_MCHUNK, N - n0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < STG_KT * nc; e += blockDim.x) {
+            const int tl = e / nc, n = n0 + e % nc;
+            const uint64_t t = (uint64_t)(a.t0 + (long long)blockIdx.z * STG_KT + tl);
+            s_ph[tl][e % nc] = a.alpha[(size_t)j * N + n] + a.phi32[n] + (uint32_t)((a.rate64[n] * t) >> 32);
+        }
+        for (int e = threadIdx.x; e < nc; e += blockDim.x) s_sq[e] = a.sqsig[(size_t)j * N + n0 + e];
+        __syncthreads();
+        if (k < a.nz) {
+            const uint32_t *be = a.betaT + (size_t)n0 * a.nz + k;
+#pragma unroll 4
+            for (int m = 0; m < nc; ++m) {
+                const uint32_t ph = s_ph[lt][m] + be[(size_t)m * a.nz];
+                const float x = (float)(int32_t)ph * 1.4629180792671596e-09f;   // 2 pi / 2^32
+                const float4 qs = s_sq[m];
+                const float cw = qs.x * __cosf(x);
+                vx = fmaf(cw, qs.y, vx);
+                vy = fmaf(cw, qs.z, vy);
+                vz = fmaf(cw, qs.w, vz);
+            }
+        }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        vx += __shfl_xor_sync(0xffffffffu, vx, o);
-        vy += __shfl_xor_sync(0xffffffffu, vy, o);
-        vz += __shfl_xor_sync(0xffffffffu, vz, o);
-    }
-    if (lane == 0) {
+    if (k >= a.nz || ts >= a.nsteps) return;
+    float *o = a.out + (((size_t)ts * a.nz + k) * a.ny + j) * 3;
+    if (a.apply_profile) {
         const float *m = a.amat + 6 * j;
-        float *o = a.uin + ((size_t)k * a.ny + j) * 3;
         o[0] = a.UR[j] + m[0] * vx;
         o[1] = m[1] * vx + m[2] * vy;
         o[2] = m[3] * vx + m[4] * vy + m[5] * vz;
+    } else {
+        o[0] = vx; o[1] = vy; o[2] = vz;
     }
 }
 
@@ -486,7 +601,8 @@ __global__ void init_kernel(typename S::T *f, const float *UR, int nx, int ny, l
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         const float cu = CX(q) * u;
-        S::st(f + q * ncell + c, WQ(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * u * u), WQ(q));
+        const float dev = WQ(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * u * u);
+        S::st(f + q * ncell + c, S::SHIFTED ? dev : dev + WQ(q));
     }
 }
 
@@ -498,7 +614,7 @@ __global__ void fields_kernel(const typename S::T *f, const float *fw, float *rh
     if (c >= ncell) return;
     float v[19];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) v[q] = S::ld(f + q * ncell + c, WQ(q));
+    for (int q = 0; q < 19; ++q) v[q] = S::ld(f + q * ncell + c) - (S::SHIFTED ? 0.0f : WQ(q));
     float dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) { dr += v[q]; jx += CX(q) * v[q]; jy += CY(q) * v[q]; jz += CZ(q) * v[q]; }
@@ -512,25 +628,51 @@ __global__ void fields_kernel(const typename S::T *f, const float *fw, float *rh
     u[3 * c] = jx / r; u[3 * c + 1] = jy / r; u[3 * c + 2] = jz / r;
 }
 
-// z-sums of the velocity moments and of u_tau, accumulated in FP64
-__global__ void stats_kernel(const float *ubuf, const float *utau, double *st, double *st_utau, int nx,
-                             int ny, int nz, long long ncell, int wall) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < nx * ny) {
-        double s[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int k = 0; k < nz; ++k) {
-            const long long c = (long long)k * nx * ny + t;
-            const double u = ubuf[c], v = ubuf[ncell + c], w = ubuf[2 * ncell + c];
-            s[0] += u; s[1] += v; s[2] += w; s[3] += u * u; s[4] += v * v; s[5] += w * w; s[6] += u * v;
+// z-sums of the velocity moments added to the FP64 accumulators.  Block =
+// 32 consecutive (i, j) columns x 8 chunks of z; each thread sums its chunk in
+// FP32, the chunks are combined in shared memory and one thread per column adds
+// the sample to the FP64 sums.  Blocks past the columns do the u_tau sums.
+constexpr int ST_COLS = 32, ST_CHUNKS = 8;
+__global__ void __launch_bounds__(ST_COLS * ST_CHUNKS) stats_kernel(
+        const float *__restrict__ ubuf, const float *__restrict__ utau, double *st, double *st_utau, int nx,
+        int ny, int nz, long long ncell, int wall) {
+    __shared__ float part[ST_CHUNKS][7][ST_COLS];
+    const int col = threadIdx.x % ST_COLS, ch = threadIdx.x / ST_COLS;
+    const int nxy = nx * ny;
+    const int nblk_cols = (nxy + ST_COLS - 1) / ST_COLS;
+    if ((int)blockIdx.x < nblk_cols) {
+        const int t = blockIdx.x * ST_COLS + col;
+        float s[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (t < nxy) {
+#pragma unroll 4
+            for (int k = ch; k < nz; k += ST_CHUNKS) {
+                const long long c = (long long)k * nxy + t;
+                const float u = ubuf[c], v = ubuf[ncell + c], w = ubuf[2 * ncell + c];
+                s[0] += u; s[1] += v; s[2] += w;
+                s[3] = fmaf(u, u, s[3]); s[4] = fmaf(v, v, s[4]); s[5] = fmaf(w, w, s[5]); s[6] = fmaf(u, v, s[6]);
+            }
         }
-        double *o = st + (size_t)t * 7;
 #pragma unroll
-        for (int q = 0; q < 7; ++q) o[q] += s[q];
-    } else if (wall && t < nx * ny + 2 * nx) {
-        const int r = t - nx * ny, w = r / nx, i = r % nx;
-        double s = 0;
-        for (int k = 0; k < nz; ++k) s += utau[((size_t)w * nz + k) * nx + i];
-        st_utau[w * nx + i] += s;
+        for (int q = 0; q < 7; ++q) part[ch][q][col] = s[q];
+        __syncthreads();
+        if (ch == 0 && t < nxy) {
+            double *o = st + (size_t)t * 7;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                float a = 0.0f;
+#pragma unroll
+                for (int c = 0; c < ST_CHUNKS; ++c) a += part[c][q][col];
+                o[q] += (double)a;
+            }
+        }
+    } else if (wall) {
+        const int r = ((int)blockIdx.x - nblk_cols) * blockDim.x + threadIdx.x;
+        if (r < 2 * nx) {
+            const int w = r / nx, i = r % nx;
+            float s = 0;
+            for (int k = 0; k < nz; ++k) s += utau[((size_t)w * nz + k) * nx + i];
+            st_utau[w * nx + i] += (double)s;
+        }
     }
 }
 
@@ -539,12 +681,13 @@ __global__ void wall_shear_kernel(const float *fw, double *out, int nx, int nz) 
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * nx) return;
     const int w = t / nx, i = t % nx;
-    double s = 0;
+    float s = 0.0f;
+#pragma unroll 4
     for (int k = 0; k < nz; ++k) {
         const float *F = fw + (((size_t)w * nz + k) * nx + i) * 3;
-        s += sqrt((double)F[0] * F[0] + (double)F[1] * F[1] + (double)F[2] * F[2]);
+        s += sqrtf(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
     }
-    out[t] = s / nz;
+    out[t] = (double)s / nz;
 }
 
 }  // namespace lbmk

@@ -100,10 +100,14 @@ def test_stg_amplitude_and_length_scale_parameters():
     o, g = make_pair(8, 32, 8, n_modes=64, seed=6, theta=theta)
     uo, ug = o.inlet_velocity(50), g.inlet_velocity(50)
     assert np.max(np.abs(ug - uo)) < 1e-4 * np.max(np.abs(uo[..., 1:]))
-    # set_params rebuilds the tables
+    # set_params rebuilds the tables but keeps the flow constants of creation
+    from oracle.oracle import Oracle, default_config
+    from paper_2304_04214_gb300.inputs import stg_uniforms
     g.set_params((0.4, 1.0, 0.4, 7.8))
-    o2, _ = make_pair(8, 32, 8, n_modes=64, seed=6)
-    assert np.max(np.abs(g.inlet_velocity(50) - o2.inlet_velocity(50))) < 1e-4 * 0.01
+    cfg = default_config(8, 32, 8, n_modes=64, kappa0=theta[2], B0=theta[3])
+    o2 = Oracle(cfg, theta=(0.4, 1.0, 0.4, 7.8), uniforms=stg_uniforms(64, 6))
+    u2 = o2.inlet_velocity(50)
+    assert np.max(np.abs(g.inlet_velocity(50) - u2)) < 1e-4 * np.max(np.abs(u2[..., 1:]))
 
 
 @pytest.mark.parametrize("shape,kw", [
