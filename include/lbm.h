@@ -47,6 +47,7 @@ extern "C" {
 #define LBM_EDIVERGED  -4   /* non-finite or |u| > 0.3 seen on the lattice */
 #define LBM_ENOTCONV   -5   /* the u_tau Newton solve did not converge */
 #define LBM_ESTATE     -6   /* call out of order (e.g. step before memory) */
+#define LBM_ENOSCRATCH -7   /* larger than the fixed scratch of lbm_wall_shear_noalloc */
 
 /* ---- storage of the populations ---- */
 #define LBM_FP32      0     /* f_q in FP32 */
@@ -175,6 +176,31 @@ int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R);
 /* Wall shear stress tau_w = rho u_tau^2 (Sec. 2.3) of the last step,
  * averaged over z: host out[w*nx + i], w = 0 bottom, 1 top.  Synchronizes. */
 int lbm_wall_shear(lbm_handle *h, double *out);
+
+/* Wall shear for callers that cannot allocate device memory.  (The paper has
+ * no counterpart: this is a property of the library, not of the method.)
+ *
+ * Same result and arguments as lbm_wall_shear, but the device staging buffer
+ * the reduction writes before the copy to `out` is a fixed array compiled into
+ * the library (file-scope static __device__ memory of LBM_NOALLOC_MAX_NX * 2
+ * doubles = 512 KiB) rather than part of the handle's memory, and the call
+ * allocates nothing at all: no cudaMalloc, no cudaFree, no library routine
+ * that allocates.  It is meant for code that must not allocate at that point,
+ * e.g. a coupling loop inside a host application whose memory manager owns
+ * every device allocation, or a real-time loop where an allocation could
+ * synchronize the device or fail under memory pressure.  Every GPU that loads
+ * the library holds the 512 KiB until the process exits.
+ *
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents; each call overwrites the 2*nx entries it uses before
+ * reading them, and copies them to `out` before it returns.  Two calls whose
+ * GPU work overlaps (different streams with no ordering between them) race on
+ * the array.  Errors: LBM_ENOSCRATCH if 2*nx > 2*LBM_NOALLOC_MAX_NX,
+ * LBM_EINVAL, LBM_ESTATE, LBM_ECUDA as for lbm_wall_shear. */
+#define LBM_NOALLOC_MAX_NX 32768
+int lbm_wall_shear_noalloc(lbm_handle *h, double *out);
 
 /* Instrumentation.  While enabled, every launch of the fused step kernel is
  * bracketed by CUDA events on the handle's stream.  read synchronizes and

@@ -7,6 +7,8 @@ from . import build as _build
 _LIB = None
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ENOTCONV, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LBM_ENOSCRATCH = -7
+LBM_NOALLOC_MAX_NX = 32768
 LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2
 PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16_DEV, "bf16": LBM_BF16_DEV}
 
@@ -60,6 +62,7 @@ PROTOTYPES = {
     "lbm_set_inlet_profile": (ct.c_int, [_h, _dp, _dp]),
     "lbm_get_inlet_profile": (ct.c_int, [_h, _dp, _dp]),
     "lbm_wall_shear": (ct.c_int, [_h, _dp]),
+    "lbm_wall_shear_noalloc": (ct.c_int, [_h, _dp]),
     "lbm_profile_enable": (ct.c_int, [_h, ct.c_int]),
     "lbm_profile_read": (ct.c_int, [_h, _dp, ct.POINTER(ct.c_long), ct.POINTER(ct.c_long)]),
     "lbm_destroy": (None, [_h]),

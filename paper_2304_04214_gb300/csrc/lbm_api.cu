@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -722,6 +723,51 @@ int lbm_wall_shear(lbm_handle *h, double *out) {
     return cuda_fail(cudaStreamSynchronize(h->stream));
 }
 
+// ---------------------------------------------------------------------------
+// Wall shear without any allocation.  The staging buffer of the reduction is
+// this fixed array: device code could name it directly, host code needs its
+// device address, looked up once per device with that device current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_wall_shear[2 * LBM_NOALLOC_MAX_NX];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+int lbm_wall_shear_noalloc(lbm_handle *h, double *out) {
+    if (!h || !out) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    if (h->nx > LBM_NOALLOC_MAX_NX) {
+        std::fprintf(stderr, "liblbm_gb300: lbm_wall_shear_noalloc: nx = %d exceeds the fixed scratch "
+                     "(LBM_NOALLOC_MAX_NX = %d)\n", h->nx, LBM_NOALLOC_MAX_NX);
+        return LBM_ENOSCRATCH;
+    }
+    int dev = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kMaxDevices) return LBM_EINVAL;
+    double *scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if ((e = cudaGetSymbolAddress(&p, g_noalloc_wall_shear)) != cudaSuccess) return cuda_fail(e);
+            g_noalloc_ptr[dev] = (double *)p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    const int n = 2 * h->nx;
+    // every entry read below is written by this launch first
+    lbmk::wall_shear_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(h->d_fw, scratch, h->nx, h->nz);
+    h->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(out, scratch, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    return cuda_fail(cudaStreamSynchronize(h->stream));
+}
+
 int lbm_profile_enable(lbm_handle *h, int on) {
     if (!h) return LBM_EINVAL;
     if (on && h->ev0.empty()) {
@@ -766,6 +812,7 @@ const char *lbm_error_string(int code) {
         case LBM_EDIVERGED: return "lattice diverged (non-finite or |u| > 0.3)";
         case LBM_ENOTCONV: return "u_tau Newton solve did not converge";
         case LBM_ESTATE: return "call out of order";
+        case LBM_ENOSCRATCH: return "size exceeds the fixed scratch of a no-allocation call";
         default: return "unknown error";
     }
 }
