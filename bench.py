@@ -294,6 +294,10 @@ def run_native(args, cfg, ws, rank, local):
     assert np.all(np.isfinite(tw.numpy()))
     ch.sync()
 
+    adjoint = None
+    if rank == 0 and not args.no_adjoint:
+        adjoint = adjoint_timing(dev)
+
     line = None
     if rank == 0:
         cpu = None
@@ -324,12 +328,47 @@ def run_native(args, cfg, ws, rank, local):
                     "h2d_bytes_per_step": 7 * ny * 4, "d2h_bytes_per_step": 2 * nx * 8},
             "gpu_launches": int(nall.value),
             "clocks": clk.summary(),
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     ch.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return line
+
+
+def adjoint_timing(dev, reps=3):
+    """Adjoint cost on the adjoint workload: Re_tau = 1000, 256x64x64, N = 100,
+    a 64-step window with a checkpoint every 8 steps, J_tau over 24 <= i < 48
+    and J_R at i = 40.  forward = 64 plain steps; the adjoint call runs the same
+    64 steps (storing checkpoints) plus the recomputation and the reverse
+    sweep; ratio = (adjoint call - forward) / forward."""
+    import torch
+    from paper_2304_04214_gb300.channel import LBMChannel
+    nx, ny, nz, N, T, K = 256, 64, 64, 100, 64, 8
+    ch = LBMChannel(nx, ny, nz, re_tau=1000.0, n_modes=N, seed=5, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    obj = (24, 48, 40)
+    ch.adjoint_step(T, K, obj)            # warm-up (binds the workspace)
+    ch.step(T)
+    torch.cuda.synchronize(dev)
+    fw, ad = [], []
+    for _ in range(reps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ch.step(T)
+        e1.record(stream)
+        e1.synchronize()
+        t0 = time.perf_counter()
+        J, dJ = ch.adjoint_step(T, K, obj)
+        ad.append((time.perf_counter() - t0) * 1e3)
+        fw.append(e0.elapsed_time(e1))
+    ch.close()
+    f, a = min(fw), min(ad)
+    return {"workload": "Re_tau=1000 channel 256x64x64, N=100, window 64, checkpoint every 8",
+            "forward_ms": round(f, 3), "adjoint_call_ms": round(a, 3),
+            "ratio": round((a - f) / f, 3), "J": J,
+            "dJ_dtheta": [float(x) for x in dJ]}
 
 
 def main():
@@ -341,6 +380,7 @@ def main():
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

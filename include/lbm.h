@@ -209,6 +209,54 @@ int lbm_wall_shear_noalloc(lbm_handle *h, double *out);
 int lbm_profile_enable(lbm_handle *h, int on);
 int lbm_profile_read(lbm_handle *h, double *ms_total, long *step_launches, long *all_launches);
 
+/* ---- Adjoint (gradients of a downstream objective) ----
+ *
+ * Objective over a window of T steps starting at the current state s_0
+ * (FP32 storage only):  J = J_tau + J_R with
+ *   J_tau = mean over the T steps and over the wall cells of both walls with
+ *           i_tau0 <= i < i_tau1 of tau_w / u_tau,ref^2 (tau_w = rho u_tau^2,
+ *           Sec. 2.3, eq:force_wm);
+ *   J_R   = sum_j ( <u'v'>(i_R, j) / u_tau,ref^2 - R12+(j) )^2, <.> the mean over
+ *           z and the T steps, <u'v'> = <uv> - <u><v>, R12+ the prescribed
+ *           inlet shear stress (Sec. 3.1, eq:cholesky input).
+ * u is the physical velocity of each collision (eq:momentum).  theta =
+ * (ell_e, amp, kappa, B): the STG length-scale factor and amplitude and the
+ * Reichardt constants (eq:reichard) of the wall model and the inlet mean. */
+typedef struct {
+    int i_tau0, i_tau1;   /* wall cells with i_tau0 <= i < i_tau1 enter J_tau */
+    int i_R;              /* x station of the Reynolds-stress mismatch */
+} lbm_objective;
+
+/* Device bytes of the adjoint workspace for a window of `window` steps with a
+ * checkpoint every `ckpt_every` steps (window a multiple of ckpt_every):
+ * window/ckpt_every checkpoint lattices, ckpt_every - 1 recomputed lattices, two
+ * adjoint lattices, u_tau of every step, the STG field and the inlet adjoint of
+ * every step. */
+int lbm_adjoint_required_bytes(const lbm_handle *h, int window, int ckpt_every, size_t *bytes);
+
+/* Bind the adjoint workspace (caller-owned, 256-byte aligned, at least
+ * lbm_adjoint_required_bytes), or dev_ptr NULL to let the library cudaMalloc it.
+ * Errors: LBM_EINVAL (bad window, storage not FP32), LBM_ENOMEM, LBM_ESTATE. */
+int lbm_adjoint_bind(lbm_handle *h, int window, int ckpt_every, void *dev_ptr, size_t bytes);
+
+/* Advance the state `window` steps (exactly as lbm_step would), evaluate J over
+ * them and its gradient by the hand-written adjoint of the fused step: store
+ * s_0 and every ckpt_every-th state, then for each segment in reverse
+ * recompute its states from the checkpoint and run the adjoint steps
+ * backwards.  *J and dJ_dtheta[4] are host FP64.  dJ/ds_0 is kept for
+ * lbm_adjoint_state_gradient.  Synchronizes. */
+int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_objective *obj, double *J,
+                     double dJ_dtheta[4]);
+
+/* dJ/ds_0 of the last lbm_adjoint_step, host FP64 [19][ncell]. */
+int lbm_adjoint_state_gradient(lbm_handle *h, double *lambda0);
+
+/* One vector-Jacobian product of the time step at the current state (which
+ * is left unchanged): given lambda_next = a row vector on s_{t+1} (host FP64
+ * [19][ncell]) return lambda_prev = lambda_next ds_{t+1}/ds_t and
+ * dtheta = lambda_next ds_{t+1}/dtheta.  Needs an adjoint workspace. */
+int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, double dtheta[4]);
+
 /* Replace the model parameters theta = (ell_e, amp, kappa, B) and rebuild
  * the tables that depend on them (the flow constants of lbm_create stay). */
 int lbm_set_params(lbm_handle *h, const double theta[4]);

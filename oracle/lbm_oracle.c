@@ -791,7 +791,8 @@ void API(objective_value)(const orc *h, double *J_re, double *J_im, double *part
     int ny = h->c.ny, nz = h->c.nz;
     double T = (double)h->obj_T;
     real ur2 = h->utau_ref * h->utau_ref;
-    real Jt = h->obj_tau / (T * 2.0 * (h->obj_i1 - h->obj_i0) * nz);
+    /* an empty wall range contributes nothing */
+    real Jt = h->obj_i1 > h->obj_i0 ? h->obj_tau / (T * 2.0 * (h->obj_i1 - h->obj_i0) * nz) : 0.0 * h->obj_tau;
     real JR = 0;
     for (int j = 0; j < ny; ++j) {
         double cnt = T * nz;

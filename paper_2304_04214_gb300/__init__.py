@@ -5,11 +5,11 @@ in include/lbm.h; this package is its thin Python binding.  Importing the
 package loads nothing: the library is opened on first use and the binding
 raises if it is missing -- there is no CPU fallback.
 """
-__all__ = ["LBMChannel", "lib"]
+__all__ = ["LBMChannel", "STGAdjoint", "lib"]
 
 
 def __getattr__(name):
-    if name == "LBMChannel":
+    if name in ("LBMChannel", "STGAdjoint"):
         from . import channel
         return getattr(channel, name)
     if name == "lib":

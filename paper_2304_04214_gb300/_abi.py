@@ -28,6 +28,10 @@ class Opts(ct.Structure):
                 ("inlet", ct.c_int), ("stats_every", ct.c_int), ("cuda_stream", ct.c_void_p)]
 
 
+class Objective(ct.Structure):
+    _fields_ = [("i_tau0", ct.c_int), ("i_tau1", ct.c_int), ("i_R", ct.c_int)]
+
+
 class LBMError(RuntimeError):
     def __init__(self, code, call):
         msg = lib().lbm_error_string(code).decode()
@@ -65,6 +69,11 @@ PROTOTYPES = {
     "lbm_wall_shear_noalloc": (ct.c_int, [_h, _dp]),
     "lbm_profile_enable": (ct.c_int, [_h, ct.c_int]),
     "lbm_profile_read": (ct.c_int, [_h, _dp, ct.POINTER(ct.c_long), ct.POINTER(ct.c_long)]),
+    "lbm_adjoint_required_bytes": (ct.c_int, [_h, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]),
+    "lbm_adjoint_bind": (ct.c_int, [_h, ct.c_int, ct.c_int, ct.c_void_p, ct.c_size_t]),
+    "lbm_adjoint_step": (ct.c_int, [_h, ct.c_int, ct.c_int, ct.POINTER(Objective), _dp, _dp]),
+    "lbm_adjoint_state_gradient": (ct.c_int, [_h, _dp]),
+    "lbm_vjp_step": (ct.c_int, [_h, _dp, _dp, _dp]),
     "lbm_destroy": (None, [_h]),
     "lbm_error_string": (ct.c_char_p, [ct.c_int]),
 }

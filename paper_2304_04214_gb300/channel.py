@@ -73,6 +73,7 @@ class LBMChannel:
             self.lib.lbm_destroy(self.h)
             self.h = None
             self.mem = None
+            self.adj_mem = None
 
     def __del__(self):
         try:
@@ -143,3 +144,82 @@ class LBMChannel:
 
     def reset_stats(self):
         _abi.check(self.lib.lbm_reset_stats(self.h), "lbm_reset_stats")
+
+    # ---- adjoint ----
+    def adjoint_bind(self, window, ckpt_every):
+        """Bind a torch-allocated adjoint workspace for windows of `window` steps."""
+        torch = self._torch
+        nbytes = ct.c_size_t()
+        _abi.check(self.lib.lbm_adjoint_required_bytes(self.h, int(window), int(ckpt_every),
+                                                       ct.byref(nbytes)), "lbm_adjoint_required_bytes")
+        self.adj_mem = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        _abi.check(self.lib.lbm_adjoint_bind(self.h, int(window), int(ckpt_every),
+                                             ct.c_void_p(self.adj_mem.data_ptr()), nbytes.value),
+                   "lbm_adjoint_bind")
+
+    def adjoint_step(self, window, ckpt_every, objective):
+        """Advance `window` steps; return J and dJ/dtheta (numpy, 4) of the
+        objective (i_tau0, i_tau1, i_R) by the adjoint with a checkpoint every
+        `ckpt_every` steps."""
+        if getattr(self, "adj_mem", None) is None or self._adj_shape != (window, ckpt_every):
+            self.adjoint_bind(window, ckpt_every)
+            self._adj_shape = (window, ckpt_every)
+        J = ct.c_double()
+        dJ = np.empty(4)
+        ob = _abi.Objective(*[int(x) for x in objective])
+        _abi.check(self.lib.lbm_adjoint_step(self.h, int(window), int(ckpt_every), ct.byref(ob),
+                                             ct.byref(J), _dptr(dJ)), "lbm_adjoint_step")
+        return J.value, dJ
+
+    _adj_shape = None
+    adj_mem = None
+
+    def adjoint_state_gradient(self):
+        lam = np.empty((Q, self.nz, self.ny, self.nx))
+        _abi.check(self.lib.lbm_adjoint_state_gradient(self.h, _dptr(lam)), "lbm_adjoint_state_gradient")
+        return lam
+
+    def vjp_step(self, lam_next):
+        """lambda_next ds_{t+1}/ds_t and lambda_next ds_{t+1}/dtheta at the current state."""
+        lam = np.ascontiguousarray(lam_next, dtype=np.float64)
+        prev = np.empty_like(lam)
+        dth = np.empty(4)
+        _abi.check(self.lib.lbm_vjp_step(self.h, _dptr(lam), _dptr(prev), _dptr(dth)), "lbm_vjp_step")
+        return prev, dth
+
+
+def _make_stg_adjoint():
+    import torch
+
+    class STGAdjoint(torch.autograd.Function):
+        """J(theta) over a window of steps with its adjoint gradient.
+
+        forward(theta, channel, window, ckpt_every, objective): sets the model
+        parameters theta = (ell_e, amp, kappa, B) (a float64 tensor of 4),
+        advances the channel `window` steps and returns J as a 0-d tensor; the
+        gradient dJ/dtheta comes from the hand-written adjoint (checkpoint every
+        `ckpt_every` steps) and is applied in backward.  The channel's state
+        moves forward by `window` steps as a side effect.
+        """
+
+        @staticmethod
+        def forward(ctx, theta, channel, window, ckpt_every, objective):
+            channel.set_params(theta.detach().cpu().double().numpy())
+            J, dJ = channel.adjoint_step(window, ckpt_every, objective)
+            ctx.save_for_backward(torch.tensor(dJ, dtype=theta.dtype, device=theta.device))
+            return torch.tensor(J, dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (dJ,) = ctx.saved_tensors
+            return grad_out * dJ, None, None, None, None
+
+    return STGAdjoint
+
+
+def __getattr__(name):
+    if name == "STGAdjoint":
+        cls = _make_stg_adjoint()
+        globals()["STGAdjoint"] = cls
+        return cls
+    raise AttributeError(name)

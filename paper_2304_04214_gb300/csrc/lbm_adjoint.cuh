@@ -1,0 +1,688 @@
+// lbm_adjoint.cuh -- hand-written adjoint (vector-Jacobian product) of one
+// fused time step, for gradients of a downstream objective with respect to the
+// state and to theta = (ell_e, amp, kappa, B).
+//
+// Forward step (state = post-collision populations, FP32):
+//   p = Pull(s_n) -> [x = 0: p = Rebuild(p_known, u_in)] -> wall force F(p, p_2)
+//     -> s_{n+1} = C(p, F).
+// Reverse: given lambda = dJ/ds_{n+1} at every cell, recompute the forward
+// values of the cell, run the chain backwards (collision, SGS closure,
+// equilibrium, Guo force, Reichardt wall model through the implicit function
+// theorem, regularized inlet) and push the adjoint of every pulled population
+// back to the cell and plane it was pulled from.  The pull is a permutation
+// except at the x faces: the inlet's unknown populations are not read (their
+// adjoint is zero), the outlet's clamped reads land on cells that the regular
+// pull also reads (their adjoint goes to a side buffer added afterwards), and
+// the two planes nobody reads get zeros.
+#pragma once
+#include "lbm_device.cuh"
+
+namespace lbmk {
+
+// adjoint of the collision inputs
+struct AdjIn {
+    float ls[9], ld[9];     // of the pair sums / differences
+    float lf9;              // of f_9
+    float lrho, ljx, ljy, ljz;   // of rho and of the momentum sum f c (before the force)
+    float lFx, lFy, lFz;    // of the force density
+};
+
+// Forward recompute and reverse of collide_mrt<false, HAS_FORCE> (FP32, f not
+// shifted).  lam: dJ/df* of the cell.  (lux, luy, luz): direct dJ/du of the
+// physical velocity (objective seeds).  Output: A (adjoint of the inputs; the
+// identity part lam itself is added by the caller).
+template <bool HAS_FORCE>
+__device__ __forceinline__ void collide_adjoint(const float (&lam)[19], const Pairs &P, float f9, float Fx,
+                                                float Fy, float Fz, float tau0, float csm18, float lux, float luy,
+                                                float luz, AdjIn &A) {
+    const float *s = P.s;
+    // ---------------- forward values ----------------
+    const float rho = 1.0f + P.drho, irho = 1.0f / rho;
+    const float rux = P.jx + 0.5f * Fx, ruy = P.jy + 0.5f * Fy, ruz = P.jz + 0.5f * Fz;
+    const float ux = rux * irho, uy = ruy * irho, uz = ruz * irho;
+    const float uxx = rux * ux, uyy = ruy * uy, uzz = ruz * uz;
+    const float usq = uxx + uyy + uzz;
+    const float Sax = s[2] + s[6] + s[8];
+    const float Sdg = (s[0] + s[4]) + (s[1] + s[3]) + (s[5] + s[7]);
+    const float n1 = -30.0f * f9 - 11.0f * Sax + 8.0f * Sdg + 11.0f * rho - 19.0f * usq;
+    const float s04 = s[0] + s[4], s13 = s[1] + s[3], s57 = s[5] + s[7];
+    const float pxx_eq = 2.0f * uxx - uyy - uzz, pww_eq = uyy - uzz;
+    const float n9 = 2.0f * s[8] - (s[2] + s[6]) - 2.0f * s04 + (s13 + s57) - pxx_eq;
+    const float n11 = (s[6] - s[2]) + (s57 - s13) - pww_eq;
+    const float n13 = (s[5] - s[7]) - rux * uy;
+    const float n14 = (s[0] - s[4]) - ruy * uz;
+    const float n15 = (s[1] - s[3]) - rux * uz;
+    const float c2 = n1 * (1.0f / 19.0f);
+    const float pxx = (c2 + n9) * (1.0f / 3.0f);
+    const float pyy = (c2 - 0.5f * n9 + 1.5f * n11) * (1.0f / 3.0f);
+    const float pzz = (c2 - 0.5f * n9 - 1.5f * n11) * (1.0f / 3.0f);
+    const float qq = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (n13 * n13 + n14 * n14 + n15 * n15);
+    const float Qh = sqrtf(qq);
+    const float Rr = sqrtf(tau0 * tau0 + csm18 * Qh * irho);
+    const float sv = 2.0f / (tau0 + Rr);
+    const float hv = 1.0f - 0.5f * sv;
+    float F9 = 0.f, F11 = 0.f, F13 = 0.f, F14 = 0.f, F15 = 0.f;
+    if (HAS_FORCE) {
+        F9 = 4.0f * ux * Fx - 2.0f * (uy * Fy + uz * Fz);
+        F11 = 2.0f * (uy * Fy - uz * Fz);
+        F13 = ux * Fy + uy * Fx; F14 = uy * Fz + uz * Fy; F15 = ux * Fz + uz * Fx;
+    }
+    // ---------------- mu = M lambda ----------------
+    float ls[9], ld[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) { ls[p] = lam[p] + lam[18 - p]; ld[p] = lam[p] - lam[18 - p]; }
+    const float l9 = lam[9];
+    const float LSax = ls[2] + ls[6] + ls[8];
+    const float LSdg = (ls[0] + ls[4]) + (ls[1] + ls[3]) + (ls[5] + ls[7]);
+    const float m1 = -30.0f * l9 - 11.0f * LSax + 8.0f * LSdg;
+    const float m2 = 12.0f * l9 - 4.0f * LSax + LSdg;
+    const float DX = (ld[3] - ld[1]) + (ld[7] - ld[5]);
+    const float DY = (ld[4] - ld[0]) - (ld[5] + ld[7]);
+    const float DZ = -(ld[0] + ld[4]) - (ld[1] + ld[3]);
+    const float m3 = DX - ld[8], m4 = DX + 4.0f * ld[8];
+    const float m5 = DY - ld[6], m6 = DY + 4.0f * ld[6];
+    const float m7 = DZ - ld[2], m8 = DZ + 4.0f * ld[2];
+    const float L04 = ls[0] + ls[4], L13 = ls[1] + ls[3], L57 = ls[5] + ls[7];
+    const float m9 = 2.0f * ls[8] - (ls[2] + ls[6]) - 2.0f * L04 + (L13 + L57);
+    const float m10 = -4.0f * ls[8] + 2.0f * (ls[2] + ls[6]) - 2.0f * L04 + (L13 + L57);
+    const float m11 = (ls[6] - ls[2]) + (L57 - L13);
+    const float m12 = 2.0f * (ls[2] - ls[6]) + (L57 - L13);
+    const float m13 = ls[5] - ls[7], m14 = ls[0] - ls[4], m15 = ls[1] - ls[3];
+    const float m16 = (ld[1] - ld[3]) + (ld[7] - ld[5]);
+    const float m17 = (ld[4] - ld[0]) + (ld[5] + ld[7]);
+    const float m18 = (ld[0] + ld[4]) - (ld[1] + ld[3]);
+    // L = lambda . f* = lambda . f - sum_k mu_k G_k  ->  a_k = dL/dG_k = -mu_k
+    // ---------------- reverse through G ----------------
+    float bn1 = -m1 * S_E / 2394.0f;
+    float bn2 = -m2 * S_EPS / 252.0f;
+    const float bn4 = -m4 * S_Q / 40.0f, bn6 = -m6 * S_Q / 40.0f, bn8 = -m8 * S_Q / 40.0f;
+    float bn9 = -m9 * sv / 36.0f;
+    const float bn10 = -m10 * S_PI / 72.0f;
+    float bn11 = -m11 * sv / 12.0f;
+    const float bn12 = -m12 * S_PI / 24.0f;
+    float bn13 = -m13 * sv * 0.25f, bn14 = -m14 * sv * 0.25f, bn15 = -m15 * sv * 0.25f;
+    const float bn16 = -m16 * S_M * 0.125f, bn17 = -m17 * S_M * 0.125f, bn18 = -m18 * S_M * 0.125f;
+    // d/dsv of (sv n - (1 - sv/2) F) = n + F/2
+    float bsv = -m9 * (n9 + 0.5f * F9) / 36.0f - m11 * (n11 + 0.5f * F11) / 12.0f
+              - (m13 * (n13 + 0.5f * F13) + m14 * (n14 + 0.5f * F14) + m15 * (n15 + 0.5f * F15)) * 0.25f;
+    float lFx = 0.f, lFy = 0.f, lFz = 0.f;
+    float lux_ = lux, luy_ = luy, luz_ = luz;
+    if (HAS_FORCE) {
+        const float cq = (1.0f - 0.5f * S_Q) * (2.0f / 3.0f);
+        const float buF = m1 * (1.0f - 0.5f * S_E) * 38.0f / 2394.0f - m2 * (1.0f - 0.5f * S_EPS) * 11.0f / 252.0f;
+        lFx += 0.1f * m3 - m4 * cq / 40.0f;
+        lFy += 0.1f * m5 - m6 * cq / 40.0f;
+        lFz += 0.1f * m7 - m8 * cq / 40.0f;
+        const float bF9 = m9 * hv / 36.0f - m10 * (1.0f - 0.5f * S_PI) * 0.5f / 72.0f;
+        const float bF11 = m11 * hv / 12.0f - m12 * (1.0f - 0.5f * S_PI) * 0.5f / 24.0f;
+        const float bF13 = m13 * hv * 0.25f, bF14 = m14 * hv * 0.25f, bF15 = m15 * hv * 0.25f;
+        // uF = u . F
+        lux_ += buF * Fx; luy_ += buF * Fy; luz_ += buF * Fz;
+        lFx += buF * ux; lFy += buF * uy; lFz += buF * uz;
+        // F9 = 4 ux Fx - 2 uy Fy - 2 uz Fz
+        lux_ += 4.0f * Fx * bF9; lFx += 4.0f * ux * bF9;
+        luy_ -= 2.0f * Fy * bF9; lFy -= 2.0f * uy * bF9;
+        luz_ -= 2.0f * Fz * bF9; lFz -= 2.0f * uz * bF9;
+        // F11 = 2 uy Fy - 2 uz Fz
+        luy_ += 2.0f * Fy * bF11; lFy += 2.0f * uy * bF11;
+        luz_ -= 2.0f * Fz * bF11; lFz -= 2.0f * uz * bF11;
+        // F13 = ux Fy + uy Fx, F14 = uy Fz + uz Fy, F15 = ux Fz + uz Fx
+        lux_ += Fy * bF13; lFy += ux * bF13; luy_ += Fx * bF13; lFx += uy * bF13;
+        luy_ += Fz * bF14; lFz += uy * bF14; luz_ += Fy * bF14; lFy += uz * bF14;
+        lux_ += Fz * bF15; lFz += ux * bF15; luz_ += Fx * bF15; lFx += uz * bF15;
+    }
+    // ---------------- SGS: sv = 2 / (tau0 + sqrt(tau0^2 + c Qh / rho)) ----------------
+    float lirho = 0.f;
+    {
+        const float lR = bsv * (-0.5f * sv * sv);
+        const float lX = lR * 0.5f / Rr;
+        const float lQh = lX * csm18 * irho;
+        lirho += lX * csm18 * Qh;
+        const float lqq = Qh > 1e-30f ? lQh * 0.5f / Qh : 0.0f;
+        const float lpxx = 2.0f * pxx * lqq, lpyy = 2.0f * pyy * lqq, lpzz = 2.0f * pzz * lqq;
+        bn13 += 4.0f * n13 * lqq; bn14 += 4.0f * n14 * lqq; bn15 += 4.0f * n15 * lqq;
+        const float lc2 = (lpxx + lpyy + lpzz) * (1.0f / 3.0f);
+        bn9 += (lpxx - 0.5f * lpyy - 0.5f * lpzz) * (1.0f / 3.0f);
+        bn11 += (1.5f * lpyy - 1.5f * lpzz) * (1.0f / 3.0f);
+        bn1 += lc2 * (1.0f / 19.0f);
+    }
+    // ---------------- n_k -> pair moments, rho, rho u ----------------
+    float las[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, lad[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    float lf9 = 0.f, lrho = 0.f, lusq = 0.f;
+    float lrux = 0.f, lruy = 0.f, lruz = 0.f, ljx = 0.f, ljy = 0.f, ljz = 0.f;
+    // n1 = e1 + 11 rho - 19 usq, n2 = e2 - 3 rho + 5.5 usq
+    lrho += 11.0f * bn1 - 3.0f * bn2;
+    lusq += -19.0f * bn1 + 5.5f * bn2;
+    lf9 += -30.0f * bn1 + 12.0f * bn2;
+    const float lSax = -11.0f * bn1 - 4.0f * bn2, lSdg = 8.0f * bn1 + bn2;
+    las[2] += lSax; las[6] += lSax; las[8] += lSax;
+    las[0] += lSdg; las[4] += lSdg; las[1] += lSdg; las[3] += lSdg; las[5] += lSdg; las[7] += lSdg;
+    // n4 = jx + 5 d8 + 2/3 rux (and y, z)
+    ljx += bn4; lad[8] += 5.0f * bn4; lrux += (2.0f / 3.0f) * bn4;
+    ljy += bn6; lad[6] += 5.0f * bn6; lruy += (2.0f / 3.0f) * bn6;
+    ljz += bn8; lad[2] += 5.0f * bn8; lruz += (2.0f / 3.0f) * bn8;
+    // n9, n10 and the equilibrium part pxx_eq
+    las[8] += 2.0f * bn9 - 4.0f * bn10;
+    las[2] += -bn9 + 2.0f * bn10; las[6] += -bn9 + 2.0f * bn10;
+    las[0] += -2.0f * bn9 - 2.0f * bn10; las[4] += -2.0f * bn9 - 2.0f * bn10;
+    las[1] += bn9 + bn10; las[3] += bn9 + bn10; las[5] += bn9 + bn10; las[7] += bn9 + bn10;
+    const float lpxxeq = -bn9 + 0.5f * bn10;
+    // n11, n12 and pww_eq
+    las[6] += bn11 - 2.0f * bn12; las[2] += -bn11 + 2.0f * bn12;
+    las[5] += bn11 + bn12; las[7] += bn11 + bn12; las[1] -= bn11 + bn12; las[3] -= bn11 + bn12;
+    const float lpwweq = -bn11 + 0.5f * bn12;
+    // n13..n15
+    las[5] += bn13; las[7] -= bn13; las[0] += bn14; las[4] -= bn14; las[1] += bn15; las[3] -= bn15;
+    const float luxy = -bn13, luyz = -bn14, luxz = -bn15;
+    // n16..n18
+    lad[1] += bn16 - bn18; lad[3] += -bn16 - bn18; lad[7] += bn16 + bn17; lad[5] += -bn16 + bn17;
+    lad[4] += bn17 + bn18; lad[0] += -bn17 + bn18;
+    // quadratic equilibrium terms: uxx = rux ux etc., uxy = rux uy, uyz = ruy uz, uxz = rux uz
+    const float luxx = lusq + 2.0f * lpxxeq, luyy = lusq - lpxxeq + lpwweq, luzz = lusq - lpxxeq - lpwweq;
+    lrux += ux * luxx + uy * luxy + uz * luxz; lux_ += rux * luxx;
+    lruy += uy * luyy + uz * luyz;             luy_ += ruy * luyy + rux * luxy;
+    lruz += uz * luzz;                         luz_ += ruz * luzz + ruy * luyz + rux * luxz;
+    // u = ru / rho
+    lrux += irho * lux_; lruy += irho * luy_; lruz += irho * luz_;
+    lirho += rux * lux_ + ruy * luy_ + ruz * luz_;
+    lrho += -irho * irho * lirho;
+    // ru = j + F/2
+    ljx += lrux; ljy += lruy; ljz += lruz;
+    if (HAS_FORCE) { lFx += 0.5f * lrux; lFy += 0.5f * lruy; lFz += 0.5f * lruz; }
+#pragma unroll
+    for (int p = 0; p < 9; ++p) { A.ls[p] = las[p]; A.ld[p] = lad[p]; }
+    A.lf9 = lf9; A.lrho = lrho; A.ljx = ljx; A.ljy = ljy; A.ljz = ljz;
+    A.lFx = lFx; A.lFy = lFy; A.lFz = lFz;
+}
+
+// lambda of the pulled populations from the adjoint of (pairs, f9, rho, j):
+// rho = 1 + sum s + f9 - 1, j from d, s_p = f_p + f_{18-p}, d_p = f_p - f_{18-p}.
+__device__ __forceinline__ void adjoint_to_pops(const float (&lam)[19], AdjIn &A, float (&lp)[19]) {
+    float ls[9], ld[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) { ls[p] = A.ls[p] + A.lrho; ld[p] = A.ld[p]; }
+    const float lf9 = A.lf9 + A.lrho;
+    // jx = (d3 - d1) + (d7 - d5) - d8 ; jy = (d4 - d0) - (d5 + d7) - d6 ; jz = -(d0 + d4) - (d1 + d3) - d2
+    ld[3] += A.ljx; ld[1] -= A.ljx; ld[7] += A.ljx; ld[5] -= A.ljx; ld[8] -= A.ljx;
+    ld[4] += A.ljy; ld[0] -= A.ljy; ld[5] -= A.ljy; ld[7] -= A.ljy; ld[6] -= A.ljy;
+    ld[0] -= A.ljz; ld[4] -= A.ljz; ld[1] -= A.ljz; ld[3] -= A.ljz; ld[2] -= A.ljz;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) { lp[p] = lam[p] + ls[p] + ld[p]; lp[18 - p] = lam[18 - p] + ls[p] - ld[p]; }
+    lp[9] = lam[9] + lf9;
+}
+
+// Reichardt law derivatives for the implicit-function theorem:
+// R(u) = u u+(y1 u / nu) - uhat; dR/du = u+ + y+ u+'; dR/dkappa = u du+/dkappa; dR/dB = u du+/dB.
+__device__ __forceinline__ void reichardt_partials(float yp, float kap, float B, float &up, float &dup, float &dk,
+                                                   float &dB) {
+    const float e11 = expf(-yp * (1.0f / 11.0f)), e3 = expf(-yp * (1.0f / 3.0f));
+    const float l1 = log1pf(kap * yp);
+    up = l1 / kap + B * (1.0f - e11 - yp * (1.0f / 11.0f) * e3);
+    dup = 1.0f / (1.0f + kap * yp) + B * (e11 * (1.0f / 11.0f) - e3 * (1.0f / 11.0f) + yp * (1.0f / 33.0f) * e3);
+    dk = -l1 / (kap * kap) + yp / (kap * (1.0f + kap * yp));
+    dB = 1.0f - e11 - yp * (1.0f / 11.0f) * e3;
+}
+
+// ---------------------------------------------------------------------------
+struct AdjArgs {
+    const float *in[19];            // s_n (FP32 f), read by pull
+    const float *__restrict__ lam;  // [19][ncell] dJ/ds_{n+1}
+    float *__restrict__ lout;       // [19][ncell] dJ/ds_n (written by push)
+    float *__restrict__ outlet;     // [5][nz][ny] clamped-outlet adjoints, added by adj_outlet_kernel
+    const float *__restrict__ utau;  // [2][nz][nx] u_tau of this step (forward result, warm start)
+    const float *__restrict__ vprime;  // [nz][ny][3] STG field of this step
+    const float *__restrict__ UR;
+    const float *__restrict__ amat;
+    float *__restrict__ luin;       // [nz][ny][3] dJ/du_in of this step (null: not needed)
+    double *__restrict__ gtheta;    // [4] accumulated dJ/dtheta (wall-model part: kappa, B)
+    // objective seeds (null: none)
+    const float *__restrict__ jr_coef;  // [ny] 2 r_j / (u_tau^2 T nz) of J_R
+    const float *__restrict__ jr_mean;  // [2][ny] <u>_j, <v>_j
+    float jtau_w;                   // dJ/dtau_w of one wall cell (J_tau weight), 0 if none
+    int i_tau0, i_tau1, i_R;
+    int nx, ny, nz;
+    int inlet, wall_model;
+    float tau0, csm18, y1_nu, kappa, B;
+};
+
+// Pull source of population q (compile-time after unrolling) from the
+// per-cell row offsets of the forward kernel: plane (mirrored at a slip wall)
+// and cell offset.
+struct PullGeom {
+    int o00, ozm, ozp, oym, oyp, ic, xm, xp;
+    bool bot, top;
+};
+__device__ __forceinline__ int src_plane(int q, const PullGeom &g) {
+    return ((CY(q) < 0 && g.top) || (CY(q) > 0 && g.bot)) ? mirror_y(q) : q;
+}
+__device__ __forceinline__ int src_off(int q, const PullGeom &g) {
+    const int oz = CZ(q) < 0 ? g.ozp : (CZ(q) > 0 ? g.ozm : 0);
+    const int oy = CY(q) < 0 ? g.oyp : (CY(q) > 0 ? g.oym : 0);
+    const int x = CX(q) < 0 ? g.xp : (CX(q) > 0 ? g.xm : g.ic);
+    return g.o00 + oy + oz + x;
+}
+
+template <bool WALLBLOCK>
+__device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int k, int tx, float (*sh)[4]) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const bool valid = i < nx;
+    const long long N = (long long)nx * ny * nz;
+    PullGeom G;
+    G.ic = valid ? i : nx - 1;
+    G.xm = G.ic - 1; G.xp = G.ic + 1;
+    if (a.inlet) { G.xm = max(G.xm, 0); G.xp = min(G.xp, nx - 1); }
+    else { G.xm = G.xm < 0 ? nx - 1 : G.xm; G.xp = G.xp >= nx ? 0 : G.xp; }
+    const int plane = nx * ny;
+    G.ozm = k == 0 ? (nz - 1) * plane : -plane;
+    G.ozp = k == nz - 1 ? -(nz - 1) * plane : plane;
+    G.bot = j == 0; G.top = j == ny - 1;
+    G.oym = G.bot ? 0 : -nx; G.oyp = G.top ? 0 : nx;
+    G.o00 = (k * ny + j) * nx;
+    // ---- forward recompute: pull ----
+    float f[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) f[q] = a.in[WALLBLOCK ? src_plane(q, G) : q][src_off(q, G)];
+    // ---- inlet rebuild (eq:f_i, eq:bc_eq, eq:f_i_neq, eq:density_bc) ----
+    const bool is_inlet = a.inlet && i == 0;
+    float vx = 0.f, vy = 0.f, vz = 0.f, rin = 1.f;
+    if (is_inlet) {
+        const float *vp = a.vprime + ((size_t)k * ny + j) * 3;
+        const float *m = a.amat + 6 * j;
+        vx = a.UR[j] + m[0] * vp[0];
+        vy = m[1] * vp[0] + m[2] * vp[1];
+        vz = m[3] * vp[0] + m[4] * vp[1] + m[5] * vp[2];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q] -= WQ(q);
+        const float sk = (f[0] + f[2] + f[4] + f[6] + f[9] + f[12] + f[14] + f[16] + f[18])
+                       + 2.0f * (f[1] + f[5] + f[8] + f[11] + f[15]);
+        rin = (1.0f + sk) / (1.0f - vx);
+        const float drin = rin - 1.0f, vv = vx * vx + vy * vy + vz * vz;
+        auto feq = [&](int q) {
+            const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
+            return WQ(q) * (drin + rin * (3.0f * cu + 4.5f * cu * cu - 1.5f * vv));
+        };
+#pragma unroll
+        for (int q = 0; q < 19; ++q) if (CX(q) <= 0) f[q] -= feq(q);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) if (CX(q) > 0) f[q] = f[18 - q];
+        float pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0, tr = 0;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            pxx += CX(q) * CX(q) * f[q]; pyy += CY(q) * CY(q) * f[q]; pzz += CZ(q) * CZ(q) * f[q];
+            pxy += CX(q) * CY(q) * f[q]; pyz += CY(q) * CZ(q) * f[q]; pxz += CX(q) * CZ(q) * f[q];
+            tr += f[q];
+        }
+        pxx -= tr * (1.0f / 3.0f); pyy -= tr * (1.0f / 3.0f); pzz -= tr * (1.0f / 3.0f);
+        const float trp = (pxx + pyy + pzz) * (1.0f / 3.0f);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const float qp = CX(q) * CX(q) * pxx + CY(q) * CY(q) * pyy + CZ(q) * CZ(q) * pzz
+                           + 2.0f * (CX(q) * CY(q) * pxy + CY(q) * CZ(q) * pyz + CX(q) * CZ(q) * pxz) - trp;
+            f[q] = feq(q) + 4.5f * WQ(q) * qp + WQ(q);
+        }
+    }
+    Pairs P;
+    make_pairs<false>(f, P);
+    const float f9 = f[9];
+    // ---- wall model forward ----
+    const bool bot = G.bot, top = G.top, is_wall = WALLBLOCK && a.wall_model && (bot || top);
+    float Fx = 0.f, Fz = 0.f;
+    float ex = 0.f, ez = 0.f, tn = 0.f, ut = 0.f, sg = 1.f, irho_w = 0.f;
+    float irho2 = 0.f, j2x = 0.f, j2z = 0.f;
+    if (WALLBLOCK && a.wall_model) {
+        if (!(bot || top)) { sh[tx][0] = P.jx; sh[tx][1] = P.jz; sh[tx][2] = 1.0f / (1.0f + P.drho); }
+        __syncthreads();
+        if (is_wall) {
+            j2x = sh[tx][0]; j2z = sh[tx][1]; irho2 = sh[tx][2];
+            const float u2x = j2x * irho2, u2z = j2z * irho2;
+            irho_w = 1.0f / (1.0f + P.drho);
+            tn = sqrtf(u2x * u2x + u2z * u2z);
+            if (tn >= 1e-12f) {
+                ex = u2x / tn; ez = u2z / tn;
+                const float uhat = (P.jx * ex + P.jz * ez) * irho_w;
+                sg = uhat < 0.0f ? -1.0f : 1.0f;
+                const float ua = fabsf(uhat);
+                if (ua > 0.0f && valid) {
+                    bool ok;
+                    const int w = bot ? 0 : 1;
+                    ut = solve_utau_dev(ua, a.y1_nu, a.kappa, a.B, a.utau[((size_t)w * nz + k) * nx + i], &ok);
+                }
+                const float tw = (1.0f + P.drho) * ut * ut * sg;
+                Fx = -tw * ex; Fz = -tw * ez;
+            }
+        }
+        __syncthreads();   // the shared slots are reused for the reverse below
+    }
+    // ---- reverse of the collision (with the objective seeds) ----
+    float lam[19];
+    const int c = G.o00 + G.ic;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) lam[q] = valid ? a.lam[q * N + c] : 0.0f;
+    float lux = 0.f, luy = 0.f;
+    if (a.jr_coef && i == a.i_R && valid) {
+        // J_R: d/du of the <u'v'> terms, u and v of this collision
+        const float rho = 1.0f + P.drho;
+        const float uu = (P.jx + 0.5f * Fx) / rho, vv = P.jy / rho;
+        const float cj = a.jr_coef[j];
+        lux = cj * (vv - a.jr_mean[ny + j]);
+        luy = cj * (uu - a.jr_mean[j]);
+    }
+    AdjIn A;
+    if (is_wall) collide_adjoint<true>(lam, P, f9, Fx, 0.f, Fz, a.tau0, a.csm18, lux, luy, 0.f, A);
+    else collide_adjoint<false>(lam, P, f9, 0.f, 0.f, 0.f, a.tau0, a.csm18, lux, luy, 0.f, A);
+
+    // ---- reverse of the wall model (implicit function theorem for u_tau) ----
+    if (WALLBLOCK && a.wall_model) {
+        float lj2x = 0.f, lj2z = 0.f, lirho2 = 0.f, gk = 0.f, gB = 0.f;
+        if (is_wall && tn >= 1e-12f && valid) {
+            const float tw = (1.0f + P.drho) * ut * ut * sg;
+            const float ltw = -(A.lFx * ex + A.lFz * ez);
+            float lex = -tw * A.lFx, lez = -tw * A.lFz;
+            // tau = rho ut^2 (unsigned), tw = tau sg; J_tau weight on tau
+            float ltau = sg * ltw;
+            if (i >= a.i_tau0 && i < a.i_tau1) ltau += a.jtau_w;
+            A.lrho += ut * ut * ltau;
+            const float lut = 2.0f * (1.0f + P.drho) * ut * ltau;
+            if (ut > 0.0f) {
+                float up, dup, dk, dB;
+                const float yp = a.y1_nu * ut;
+                reichardt_partials(yp, a.kappa, a.B, up, dup, dk, dB);
+                const float Ru = up + yp * dup;
+                const float lua = lut / Ru;
+                gk = -lut * ut * dk / Ru;
+                gB = -lut * ut * dB / Ru;
+                const float luh = sg * lua;
+                // uhat = (jx ex + jz ez) irho_w
+                A.ljx += ex * irho_w * luh; A.ljz += ez * irho_w * luh;
+                lex += P.jx * irho_w * luh; lez += P.jz * irho_w * luh;
+                const float lirw = (P.jx * ex + P.jz * ez) * luh;
+                A.lrho += -irho_w * irho_w * lirw;
+            }
+            // e = t / |t|, t = (u2x, u2z)
+            const float dot = lex * ex + lez * ez;
+            const float lu2x = (lex - dot * ex) / tn, lu2z = (lez - dot * ez) / tn;
+            // u2 = j2 irho2
+            lj2x = irho2 * lu2x; lj2z = irho2 * lu2z;
+            lirho2 = j2x * lu2x + j2z * lu2z;
+        }
+        if (is_wall) { sh[tx][0] = lj2x; sh[tx][1] = lj2z; sh[tx][2] = lirho2; }
+        __syncthreads();
+        if (!(bot || top)) {
+            const float li2 = sh[tx][2];
+            const float ir = 1.0f / (1.0f + P.drho);
+            A.ljx += sh[tx][0]; A.ljz += sh[tx][1];
+            A.lrho += -ir * ir * li2;
+        }
+        // theta gradient of the wall model: warp reduction, one atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gk += __shfl_xor_sync(0xffffffffu, gk, o);
+            gB += __shfl_xor_sync(0xffffffffu, gB, o);
+        }
+        if ((threadIdx.x & 31) == 0 && (gk != 0.f || gB != 0.f)) {
+            atomicAdd(a.gtheta + 2, (double)gk);
+            atomicAdd(a.gtheta + 3, (double)gB);
+        }
+    }
+    if (!valid) return;
+    float lp[19];
+    adjoint_to_pops(lam, A, lp);
+
+    // ---- reverse of the inlet rebuild ----
+    if (is_inlet) {
+        const float drin = rin - 1.0f, vv = vx * vx + vy * vy + vz * vz;
+        // out_q = fe_q + 4.5 w_q (c c : Pi - tr Pi / 3) + w_q
+        float lPxx = 0, lPyy = 0, lPzz = 0, lPxy = 0, lPyz = 0, lPxz = 0;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const float lq = 4.5f * WQ(q) * lp[q];
+            lPxx += (CX(q) * CX(q) - 1.0f / 3.0f) * lq; lPyy += (CY(q) * CY(q) - 1.0f / 3.0f) * lq;
+            lPzz += (CZ(q) * CZ(q) - 1.0f / 3.0f) * lq;
+            lPxy += 2.0f * CX(q) * CY(q) * lq; lPyz += 2.0f * CY(q) * CZ(q) * lq; lPxz += 2.0f * CX(q) * CZ(q) * lq;
+        }
+        // Pi = sum c c fn - I tr/3: adjoint of fn_q (kept in f[])
+        const float ltr = -(lPxx + lPyy + lPzz) * (1.0f / 3.0f);
+#pragma unroll
+        for (int q = 0; q < 19; ++q)
+            f[q] = CX(q) * CX(q) * lPxx + CY(q) * CY(q) * lPyy + CZ(q) * CZ(q) * lPzz
+                 + CX(q) * CY(q) * lPxy + CY(q) * CZ(q) * lPyz + CX(q) * CZ(q) * lPxz + ltr;
+        // unknown populations copied f^neq of the opposite one
+#pragma unroll
+        for (int q = 0; q < 19; ++q) if (CX(q) > 0) { f[18 - q] += f[q]; f[q] = 0.0f; }
+        // fn = fin - fe for the known ones; fe also enters out directly:
+        // lfe = lp - lfn, lfin = lfn
+        float lrin = 0.f, lvx = 0.f, lvy = 0.f, lvz = 0.f, lvv = 0.f;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const float lfe = lp[q] - f[q];
+            const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
+            lrin += WQ(q) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * vv) * lfe;
+            const float lcu = WQ(q) * rin * (3.0f + 9.0f * cu) * lfe;
+            lvx += CX(q) * lcu; lvy += CY(q) * lcu; lvz += CZ(q) * lcu;
+            lvv += -1.5f * WQ(q) * rin * lfe;
+        }
+        (void)drin;
+        lvx += 2.0f * vx * lvv; lvy += 2.0f * vy * lvv; lvz += 2.0f * vz * lvv;
+        // rin = (1 + sk) / (1 - vx), sk = sum_{c_x=0} fin + 2 sum_{c_x<0} fin
+        const float lsk = lrin / (1.0f - vx);
+        lvx += lrin * rin / (1.0f - vx);
+#pragma unroll
+        for (int q = 0; q < 19; ++q)
+            lp[q] = CX(q) > 0 ? 0.0f : f[q] + (CX(q) == 0 ? lsk : 2.0f * lsk);
+        if (a.luin) {
+            float *o = a.luin + ((size_t)k * ny + j) * 3;
+            o[0] = lvx; o[1] = lvy; o[2] = lvz;
+        }
+    }
+
+    // ---- push the adjoint back to the pull sources ----
+    const bool is_outlet = a.inlet && i == nx - 1;
+    int oslot = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        if (is_inlet && CX(q) > 0) continue;                       // unknown: not read
+        if (is_outlet && CX(q) < 0) {                              // clamped read: shared target
+            a.outlet[((size_t)oslot * nz + k) * ny + j] = lp[q];
+            ++oslot;
+            continue;
+        }
+        a.lout[(size_t)(WALLBLOCK ? src_plane(q, G) : q) * N + src_off(q, G)] = lp[q];
+    }
+    // planes nobody reads: c_x = -1 at x = 0 and c_x = +1 at x = nx-1
+    if (is_inlet) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) if (CX(q) < 0) a.lout[(size_t)q * N + c] = 0.0f;
+    }
+    if (is_outlet) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) if (CX(q) > 0) a.lout[(size_t)q * N + c] = 0.0f;
+    }
+}
+
+template <bool W>
+__device__ __noinline__ void adjoint_cell_wall(const AdjArgs &a, int i, int j, int k, int tx, float (*sh)[4]) {
+    adjoint_cell<true>(a, i, j, k, tx, sh);
+}
+
+__global__ void __launch_bounds__(128, 4) adjoint_kernel(const __grid_constant__ AdjArgs a) {
+    __shared__ float sh[128 / BY][4];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (blockIdx.y == 0 || blockIdx.y == gridDim.y - 1) adjoint_cell_wall<true>(a, i, j, k, threadIdx.x, sh);
+    else adjoint_cell<false>(a, i, j, k, threadIdx.x, sh);
+}
+
+// The clamped outlet reads: the outlet cell's c_x < 0 populations were pulled
+// from the outlet column itself, which the regular pull of x = nx-2 also
+// reads; add their adjoint there.
+__global__ void adj_outlet_kernel(float *lout, const float *outlet, int nx, int ny, int nz) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ny * nz) return;
+    const int j = t % ny, k = t / ny;
+    const long long N = (long long)nx * ny * nz;
+    int slot = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        if (CX(q) >= 0) continue;
+        int pl, off;
+        pull_source(q, nx - 1, j, k, nx, ny, nz, 1, pl, off);
+        lout[(size_t)pl * N + off] += outlet[((size_t)slot * nz + k) * ny + j];
+        ++slot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// theta gradient through the inlet velocity, u_in = U_R(j; kappa, B) +
+// amp a(j) v'(j, k, t; ell_e) (eq:u_couple, eq:v_fluc, eq:aux_vec):
+//   dJ/d amp   += luin . (a v'),            dJ/d ell_e += luin . (amp a dv'/d ell_e),
+//   dJ/d kappa += luin_x dU_R/d kappa,      dJ/d B     += luin_x dU_R/d B.
+// k_n and the time phase scale with 1/max l_e, so d(arg_n)/d ell_e =
+// -(d max l_e / d ell_e) / max l_e * Theta_n with Theta_n = k_n (d_y y + d_z z) -
+// 2 pi nu_n t the unreduced phase; d sqrt(6 q_n)/d ell_e comes from the host.
+// Same blocking as stg_kernel (row j, 32 z x 8 time levels).
+// ---------------------------------------------------------------------------
+struct StgAdjArgs {
+    const uint32_t *__restrict__ alpha;   // [ny][N]
+    const uint32_t *__restrict__ betaT;   // [N][nz]
+    const uint32_t *__restrict__ phi32;   // [N]
+    const uint64_t *__restrict__ rate64;  // [N]
+    const float4 *__restrict__ sqsig;     // [ny][N]
+    const float *__restrict__ dsq;        // [ny][N] d sqrt(6 q_n) / d ell_e
+    const float4 *__restrict__ kphase;    // [N] (k_n d_ny, k_n d_nz, 2 pi nu_n, 0)
+    const float *__restrict__ aunit;      // [ny][6] Cholesky factor without amp
+    const float *__restrict__ dUR;        // [2][ny] dU_R/dkappa, dU_R/dB
+    const float *__restrict__ luin;       // [T][nz][ny][3]
+    double *__restrict__ gtheta;          // [4]
+    float amp, cell_scale;                // amp, (d max l_e / d ell_e) / max l_e
+    long long t0;
+    int nsteps, ny, nz, n_modes;
+};
+
+__global__ void __launch_bounds__(STG_KZ * STG_KT) stg_adjoint_kernel(const __grid_constant__ StgAdjArgs a) {
+    __shared__ uint32_t s_ph[STG_KT][STG_MCHUNK];
+    __shared__ float4 s_sq[STG_MCHUNK];
+    __shared__ float s_dsq[STG_MCHUNK];
+    __shared__ float4 s_kp[STG_MCHUNK];
+    __shared__ float s_red[4][STG_KZ * STG_KT / 32];
+    const int j = blockIdx.y;
+    const int lz = threadIdx.x % STG_KZ, lt = threadIdx.x / STG_KZ;
+    const int k = blockIdx.x * STG_KZ + lz;
+    const int ts = blockIdx.z * STG_KT + lt;
+    const int N = a.n_modes;
+    const float t = (float)(a.t0 + ts);
+    const float y = j + 0.5f, z = k + 0.5f;
+    float vx = 0.f, vy = 0.f, vz = 0.f, wx = 0.f, wy = 0.f, wz = 0.f;
+    for (int n0 = 0; n0 < N; n0 += STG_MCHUNK) {
+        const int nc = min(STG_MCHUNK, N - n0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < STG_KT * nc; e += blockDim.x) {
+            const int tl = e / nc, n = n0 + e % nc;
+            const uint64_t tt = (uint64_t)(a.t0 + (long long)blockIdx.z * STG_KT + tl);
+            s_ph[tl][e % nc] = a.alpha[(size_t)j * N + n] + a.phi32[n] + (uint32_t)((a.rate64[n] * tt) >> 32);
+        }
+        for (int e = threadIdx.x; e < nc; e += blockDim.x) {
+            s_sq[e] = a.sqsig[(size_t)j * N + n0 + e];
+            s_dsq[e] = a.dsq[(size_t)j * N + n0 + e];
+            s_kp[e] = a.kphase[n0 + e];
+        }
+        __syncthreads();
+        if (k < a.nz) {
+            const uint32_t *be = a.betaT + (size_t)n0 * a.nz + k;
+            for (int m = 0; m < nc; ++m) {
+                const uint32_t ph = s_ph[lt][m] + be[(size_t)m * a.nz];
+                const float x = (float)(int32_t)ph * 1.4629180792671596e-09f;
+                float sn, cs;
+                __sincosf(x, &sn, &cs);
+                const float4 qs = s_sq[m];
+                const float4 kp = s_kp[m];
+                const float Th = kp.x * y + kp.y * z - kp.z * t;
+                const float cw = qs.x * cs;
+                const float dw = s_dsq[m] * cs + qs.x * a.cell_scale * Th * sn;
+                vx = fmaf(cw, qs.y, vx); vy = fmaf(cw, qs.z, vy); vz = fmaf(cw, qs.w, vz);
+                wx = fmaf(dw, qs.y, wx); wy = fmaf(dw, qs.z, wy); wz = fmaf(dw, qs.w, wz);
+            }
+        }
+    }
+    float g[4] = {0.f, 0.f, 0.f, 0.f};
+    if (k < a.nz && ts < a.nsteps) {
+        const float *L = a.luin + (((size_t)ts * a.nz + k) * a.ny + j) * 3;
+        const float *m = a.aunit + 6 * j;
+        const float ax = m[0] * vx, ay = m[1] * vx + m[2] * vy, az = m[3] * vx + m[4] * vy + m[5] * vz;
+        const float bx = m[0] * wx, by = m[1] * wx + m[2] * wy, bz = m[3] * wx + m[4] * wy + m[5] * wz;
+        g[0] = a.amp * (L[0] * bx + L[1] * by + L[2] * bz);
+        g[1] = L[0] * ax + L[1] * ay + L[2] * az;
+        g[2] = L[0] * a.dUR[j];
+        g[3] = L[0] * a.dUR[a.ny + j];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g[c] += __shfl_xor_sync(0xffffffffu, g[c], o);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s_red[c][warp] = g[c];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double acc = 0.0;
+        for (int w = 0; w < STG_KZ * STG_KT / 32; ++w) acc += s_red[threadIdx.x][w];
+        atomicAdd(a.gtheta + threadIdx.x, acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Objective sums of one step, from the new post-collision state: the wall shear
+// |F_w| = rho u_tau^2 of the wall cells with i0 <= i < i1, and at x = iR the
+// z-sums of u, v and u v with rho u = sum f* c - F/2.  acc[0] = tau sum,
+// acc[1 + 3 j + (0,1,2)] = (u, v, uv) sums.  Blocks 0 .. ny-1: one row j each,
+// threads over z; the remaining blocks: the wall cells, one atomic per block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) objective_kernel(const float *__restrict__ f, const float *__restrict__ fw,
+                                                        double *acc, int nx, int ny, int nz, int i0, int i1,
+                                                        int iR) {
+    __shared__ double red[3][128];
+    const long long N = (long long)nx * ny * nz;
+    const int tid = threadIdx.x;
+    if ((int)blockIdx.x < ny) {
+        const int j = blockIdx.x;
+        double su = 0, sv = 0, suv = 0;
+        for (int k = tid; k < nz; k += blockDim.x) {
+            const long long c = ((long long)k * ny + j) * nx + iR;
+            float r = 0, jx = 0, jy = 0;
+#pragma unroll
+            for (int q = 0; q < 19; ++q) { const float v = f[q * N + c]; r += v; jx += CX(q) * v; jy += CY(q) * v; }
+            if (j == 0 || j == ny - 1) {
+                const float *F = fw + (((size_t)(j == 0 ? 0 : 1) * nz + k) * nx + iR) * 3;
+                jx -= 0.5f * F[0]; jy -= 0.5f * F[1];
+            }
+            const double u = jx / r, v = jy / r;
+            su += u; sv += v; suv += u * v;
+        }
+        red[0][tid] = su; red[1][tid] = sv; red[2][tid] = suv;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (tid < o) { red[0][tid] += red[0][tid + o]; red[1][tid] += red[1][tid + o]; red[2][tid] += red[2][tid + o]; }
+            __syncthreads();
+        }
+        if (tid == 0) { acc[1 + 3 * j] += red[0][0]; acc[2 + 3 * j] += red[1][0]; acc[3 + 3 * j] += red[2][0]; }
+        return;
+    }
+    const int w_i = i1 - i0;
+    const int e = ((int)blockIdx.x - ny) * blockDim.x + tid;
+    double s = 0.0;
+    if (w_i > 0 && e < 2 * nz * w_i) {
+        const int ii = i0 + e % w_i, r = e / w_i, k = r % nz, w = r / nz;
+        const float *F = fw + (((size_t)w * nz + k) * nx + ii) * 3;
+        s = sqrtf(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    }
+    red[0][tid] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) red[0][tid] += red[0][tid + o];
+        __syncthreads();
+    }
+    if (tid == 0 && red[0][0] != 0.0) atomicAdd(acc, red[0][0]);
+}
+
+}  // namespace lbmk

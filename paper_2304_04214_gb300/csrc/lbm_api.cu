@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_adjoint.cuh"
 #include "lbm_device.cuh"
 
 namespace {
@@ -46,7 +47,46 @@ uint32_t turns32(double turns) {
     return (uint32_t)(uint64_t)v;
 }
 
+// Forward-mode dual number (value, derivative) for the derivative tables of
+// the adjoint: d/d ell_e of the STG spectrum and of max l_e.
+struct Dual {
+    double v = 0.0, d = 0.0;
+    Dual() = default;
+    Dual(double v_, double d_ = 0.0) : v(v_), d(d_) {}
+};
+inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+inline Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+inline Dual operator/(Dual a, Dual b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+inline Dual dexp(Dual a) { const double e = std::exp(a.v); return {e, e * a.d}; }
+inline Dual dsqrt(Dual a) { const double r = std::sqrt(a.v); return {r, a.d / (2.0 * r)}; }
+inline Dual dtanh(Dual a) { const double t = std::tanh(a.v); return {t, (1.0 - t * t) * a.d}; }
+inline Dual dpow(Dual a, double e) { const double p = std::pow(a.v, e); return {p, e * std::pow(a.v, e - 1.0) * a.d}; }
+inline double dexp(double a) { return std::exp(a); }
+inline double dsqrt(double a) { return std::sqrt(a); }
+inline double dtanh(double a) { return std::tanh(a); }
+inline double dpow(double a, double e) { return std::pow(a, e); }
+inline double val(double a) { return a; }
+inline double val(Dual a) { return a.v; }
+
 }  // namespace
+
+struct lbm_handle;
+
+// Adjoint workspace (FP32 lattices, window T, checkpoint every K steps).
+struct AdjointWork {
+    bool bound = false, owns = false;
+    void *mem = nullptr;
+    int T = 0, K = 0;
+    float *ckpt = nullptr, *seg = nullptr, *lamA = nullptr, *lamB = nullptr, *outlet = nullptr;
+    float *ut_init = nullptr, *uthist = nullptr, *ut_scr = nullptr, *fw_scr = nullptr;
+    float *vwin = nullptr, *luin = nullptr, *jr_coef = nullptr, *jr_mean = nullptr;
+    float *dsq = nullptr, *aunit = nullptr, *dUR = nullptr;
+    float4 *kphase = nullptr;
+    double *gtheta = nullptr, *objacc = nullptr;
+    float cell_scale = 0.f;
+    bool have_lambda0 = false;
+};
 
 struct lbm_handle {
     int nx = 0, ny = 0, nz = 0;
@@ -199,25 +239,12 @@ struct lbm_handle {
         betaT.assign((size_t)nz * NN, 0u);
         for (int k = 0; k < nz; ++k)
             for (int n = 0; n < N; ++n) betaT[(size_t)n * nz + k] = turns32(kn[n] * dz[n] * (k + 0.5) / (2 * kPi));
-        // q_n(y) from the modified von Karman spectrum with Kolmogorov and
-        // grid cut-offs; sqrt(6 q_n) stored (the sqrt6 of eq:aux_vec folded in)
-        const double kcut = kPi;                        // 2 pi / (2 dx)
-        std::vector<double> E(N);
-        for (int j = 0; j < ny; ++j) {
-            const double d = dwall(j), ke = 2.0 * kPi / ell[j];
-            const double eps = utau_ref * utau_ref * utau_ref / (opts_kappa0 * d);
-            const double keta = 2.0 * kPi * std::pow(eps / (nu * nu * nu), 0.25);
-            double tot = 0;
-            for (int n = 0; n < N; ++n) {
-                const double k = kn[n], r = k / ke;
-                const double dk = k * (1.0 - 1.0 / k_ratio);
-                const double xc = 4.0 * std::max(k - 0.9 * kcut, 0.0) / kcut;
-                E[n] = r * r * r * r / std::pow(1.0 + 2.4 * r * r, 17.0 / 6.0) *
-                       std::exp(-(12.0 * k / keta) * (12.0 * k / keta)) * std::exp(-xc * xc * xc) * dk;
-                tot += E[n];
-            }
-            for (int n = 0; n < N; ++n) sq[(size_t)j * N + n] = (float)std::sqrt(6.0 * E[n] / tot);
-        }
+        // sqrt(6 q_n(y)) from the modified von Karman spectrum (the sqrt6 of
+        // eq:aux_vec folded in)
+        std::vector<double> sq6;
+        double mx = 0.0;
+        spectrum<double>(ell_e, sq6, mx);
+        for (size_t c = 0; c < sq6.size(); ++c) sq[c] = (float)sq6[c];
         sqsig.assign(4 * (size_t)ny * NN, 0.f);
         for (int j = 0; j < ny; ++j)
             for (int n = 0; n < N; ++n) {
@@ -227,6 +254,132 @@ struct lbm_handle {
             }
     }
     double opts_kappa0 = 0.4;   // the creation-time kappa (dissipation estimate of the spectrum)
+    AdjointWork adj;
+    // host copies of the derivative tables (built with the adjoint workspace)
+    std::vector<float> h_dsq, h_aunit, h_dUR, h_kphase;
+    float h_cell_scale = 0.f;
+
+    // sqrt(6 q_n(y)) of the modified von Karman spectrum (Sec. 3.1, cited STG
+    // method) in scalar type T, with ell_e as the independent variable.
+    template <class T>
+    void spectrum(T ell_e, std::vector<T> &out, T &maxl_out) const {
+        const int N = n_modes;
+        std::vector<T> ell(ny);
+        T mx(0.0);
+        for (int j = 0; j < ny; ++j) {
+            ell[j] = ell_e * T(delta) * dtanh(T(2.0 * dwall(j)) / (ell_e * T(delta)));
+            if (j == 0 || val(ell[j]) > val(mx)) mx = ell[j];
+        }
+        maxl_out = mx;
+        const T kmin = T(beta_kmin * 2.0 * kPi) / mx;
+        const double kcut = kPi;
+        out.assign((size_t)ny * N, T(0.0));
+        std::vector<T> E(N);
+        for (int j = 0; j < ny; ++j) {
+            const double d = dwall(j);
+            const T ke = T(2.0 * kPi) / ell[j];
+            const double eps = utau_ref * utau_ref * utau_ref / (opts_kappa0 * d);
+            const double keta = 2.0 * kPi * std::pow(eps / (nu * nu * nu), 0.25);
+            T tot(0.0);
+            for (int n = 0; n < N; ++n) {
+                const T k = kmin * T(std::pow(k_ratio, n));
+                const T r = k / ke;
+                const T dk = k * T(1.0 - 1.0 / k_ratio);
+                const double over = std::max(val(k) - 0.9 * kcut, 0.0);
+                T xc = val(k) > 0.9 * kcut ? T(4.0) * (k - T(0.9 * kcut)) / T(kcut) : T(0.0);
+                (void)over;
+                const T g = T(12.0) * k / T(keta);
+                E[n] = r * r * r * r / dpow(T(1.0) + T(2.4) * r * r, 17.0 / 6.0) * dexp(T(0.0) - g * g) *
+                       dexp(T(0.0) - xc * xc * xc) * dk;
+                tot = tot + E[n];
+            }
+            for (int n = 0; n < N; ++n) out[(size_t)j * N + n] = dsqrt(T(6.0) * E[n] / tot);
+        }
+    }
+
+    // derivative tables of the inlet velocity for the adjoint
+    void adjoint_tables() {
+        const int N = n_modes > 0 ? n_modes : 1;
+        h_dsq.assign((size_t)ny * N, 0.f);
+        h_kphase.assign(4 * (size_t)N, 0.f);
+        h_aunit.assign(6 * (size_t)ny, 0.f);
+        h_dUR.assign(2 * (size_t)ny, 0.f);
+        h_cell_scale = 0.f;
+        if (n_modes > 0) {
+            std::vector<Dual> sqd;
+            Dual mx;
+            spectrum<Dual>(Dual(theta[0], 1.0), sqd, mx);
+            for (size_t c = 0; c < sqd.size(); ++c) h_dsq[c] = (float)sqd[c].d;
+            h_cell_scale = (float)(mx.d / mx.v);
+            const double kmin = beta_kmin * 2.0 * kPi / mx.v;
+            for (int n = 0; n < n_modes; ++n) {
+                const double kn = kmin * std::pow(k_ratio, n);
+                const double *U = &uniforms[4 * (size_t)n];
+                const double ct = 1.0 - 2.0 * U[0], st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+                const double az = 2.0 * kPi * U[1];
+                const double dx = st * std::cos(az), dy = st * std::sin(az), dz = ct;
+                h_kphase[4 * n + 0] = (float)(kn * dy);
+                h_kphase[4 * n + 1] = (float)(kn * dz);
+                h_kphase[4 * n + 2] = (float)(2.0 * kPi * dx * opts.u_bulk / mx.v);
+            }
+        }
+        for (int j = 0; j < ny; ++j) {
+            const double *R = &prof_R[6 * (size_t)j];
+            const double l11 = std::sqrt(R[0]), l21 = R[3] / l11, l31 = R[4] / l11;
+            const double l22 = std::sqrt(R[1] - l21 * l21), l32 = (R[5] - l21 * l31) / l22;
+            const double l33 = std::sqrt(R[2] - l31 * l31 - l32 * l32);
+            const double L[6] = {l11, l21, l22, l31, l32, l33};
+            for (int c = 0; c < 6; ++c) h_aunit[6 * (size_t)j + c] = (float)L[c];
+            if (!custom_profile) {
+                // U_R = u_tau u+(y+; kappa, B): du+/dkappa, du+/dB at fixed y+
+                const double yp = dwall(j) * utau_ref / nu, kap = theta[2];
+                const double dk = -std::log1p(kap * yp) / (kap * kap) + yp / (kap * (1.0 + kap * yp));
+                const double dB = 1.0 - std::exp(-yp / 11.0) - yp / 11.0 * std::exp(-yp / 3.0);
+                h_dUR[j] = (float)(utau_ref * dk);
+                h_dUR[ny + j] = (float)(utau_ref * dB);
+            }
+        }
+    }
+
+    size_t adjoint_layout(Arena &ar, int T, int K) {
+        const size_t L = 19 * (size_t)ncell, W = 2 * (size_t)nz * nx, I = 3 * (size_t)nz * ny;
+        const size_t N = n_modes > 0 ? n_modes : 1;
+        adj.ckpt = ar.take<float>(L * (T / K));
+        adj.seg = ar.take<float>(L * (K - 1));
+        adj.lamA = ar.take<float>(L);
+        adj.lamB = ar.take<float>(L);
+        adj.outlet = ar.take<float>(5 * (size_t)nz * ny);
+        adj.ut_init = ar.take<float>(W);
+        adj.uthist = ar.take<float>(W * T);
+        adj.ut_scr = ar.take<float>(W);
+        adj.fw_scr = ar.take<float>(3 * W);
+        adj.vwin = ar.take<float>(I * T);
+        adj.luin = ar.take<float>(I * T);
+        adj.jr_coef = ar.take<float>(ny);
+        adj.jr_mean = ar.take<float>(2 * (size_t)ny);
+        adj.dsq = ar.take<float>((size_t)ny * N);
+        adj.aunit = ar.take<float>(6 * (size_t)ny);
+        adj.dUR = ar.take<float>(2 * (size_t)ny);
+        adj.kphase = ar.take<float4>(N);
+        adj.gtheta = ar.take<double>(4);
+        adj.objacc = ar.take<double>(1 + 3 * (size_t)ny);
+        return (ar.off + 255) & ~size_t(255);
+    }
+
+    cudaError_t upload_adjoint_tables() {
+        adjoint_tables();
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(adj.dsq, h_dsq.data(), h_dsq.size() * 4, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpyAsync(adj.kphase, h_kphase.data(), h_kphase.size() * 4, cudaMemcpyHostToDevice, stream)) !=
+            cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(adj.aunit, h_aunit.data(), h_aunit.size() * 4, cudaMemcpyHostToDevice, stream)) !=
+            cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(adj.dUR, h_dUR.data(), h_dUR.size() * 4, cudaMemcpyHostToDevice, stream)) !=
+            cudaSuccess) return e;
+        adj.cell_scale = h_cell_scale;
+        return cudaStreamSynchronize(stream);
+    }
 
     // U_R and amp * chol(R) per row (eq:cholesky); false if R is not SPD
     bool profile_tables(double amp) {
@@ -293,20 +446,31 @@ size_t prof_slot(lbm_handle *h) {
     return slot;
 }
 
+// Where one step reads and writes: state in / out, wall buffers, STG field.
+struct StepIO {
+    const void *in;
+    void *out;
+    const float *utau_in = nullptr;   // warm start; null: utau itself
+    float *utau, *fw;
+    const float *vprime;
+    bool stats;
+};
+
 template <class S>
-void launch_step_t(lbm_handle *h, bool stats) {
+void launch_step_t(lbm_handle *h, const StepIO &io) {
     using T = typename S::T;
     lbmk::StepArgs<S> a;
     const size_t N = (size_t)h->ncell;
     for (int q = 0; q < 19; ++q) {
-        a.in[q] = (const T *)h->lat[h->cur] + q * N;
-        a.out[q] = (T *)h->lat[h->cur ^ 1] + q * N;
+        a.in[q] = (const T *)io.in + q * N;
+        a.out[q] = (T *)io.out + q * N;
     }
-    a.vprime = h->d_uin + 3 * (size_t)h->nz * h->ny * (size_t)(h->t - h->stg_t0);
+    a.vprime = io.vprime;
     a.UR = h->d_UR;
     a.amat = h->d_amat;
-    a.utau = h->d_utau;
-    a.fw = h->d_fw;
+    a.utau_in = io.utau_in ? io.utau_in : io.utau;
+    a.utau = io.utau;
+    a.fw = io.fw;
     a.ubuf = h->d_ubuf;
     a.flags = h->d_flags;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
@@ -322,10 +486,18 @@ void launch_step_t(lbm_handle *h, bool stats) {
     dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
     const size_t slot = h->prof_on ? prof_slot(h) : 0;
     if (h->prof_on) cudaEventRecord(h->ev0[slot], h->stream);
-    if (stats) lbmk::step_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
+    if (io.stats) lbmk::step_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
     else lbmk::step_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
     if (h->prof_on) cudaEventRecord(h->ev1[slot], h->stream);
     h->launches += 1;
+}
+
+void launch_step_io(lbm_handle *h, const StepIO &io) {
+    switch (h->opts.precision) {
+        case LBM_FP16_DEV: launch_step_t<lbmk::StoreF16>(h, io); break;
+        case LBM_BF16_DEV: launch_step_t<lbmk::StoreBF16>(h, io); break;
+        default: launch_step_t<lbmk::StoreF32>(h, io); break;
+    }
 }
 
 // STG inlet velocities of steps t0 .. t0 + n - 1 into the ring slots 0 .. n-1.
@@ -351,11 +523,14 @@ int one_step(lbm_handle *h) {
         h->stg_len = h->stg_ring;
         launch_stg(h, h->stg_t0, h->stg_ring, false);
     }
-    switch (h->opts.precision) {
-        case LBM_FP16_DEV: launch_step_t<lbmk::StoreF16>(h, stats); break;
-        case LBM_BF16_DEV: launch_step_t<lbmk::StoreBF16>(h, stats); break;
-        default: launch_step_t<lbmk::StoreF32>(h, stats); break;
-    }
+    StepIO io;
+    io.in = h->lat[h->cur];
+    io.out = h->lat[h->cur ^ 1];
+    io.utau = h->d_utau;
+    io.fw = h->d_fw;
+    io.vprime = h->opts.inlet ? h->d_uin + 3 * (size_t)h->nz * h->ny * (size_t)(h->t - h->stg_t0) : h->d_uin;
+    io.stats = stats;
+    launch_step_io(h, io);
     if (stats) {
         h->n_samples += 1;
         const int cols = (h->nx * h->ny + lbmk::ST_COLS - 1) / lbmk::ST_COLS;
@@ -368,6 +543,62 @@ int one_step(lbm_handle *h) {
     h->cur ^= 1;
     h->t += 1;
     return cuda_fail(cudaGetLastError());
+}
+
+// STG field v' of steps t0 .. t0 + n - 1 into an explicit buffer
+void launch_stg_into(lbm_handle *h, float *out, long long t0, int n) {
+    lbmk::StgArgs a;
+    a.alpha = h->d_alpha; a.betaT = h->d_betaT; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
+    a.sqsig = h->d_sqsig; a.amat = h->d_amat; a.UR = h->d_UR; a.out = out;
+    a.t0 = t0; a.nsteps = n; a.apply_profile = 0;
+    a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
+    dim3 grid((h->nz + lbmk::STG_KZ - 1) / lbmk::STG_KZ, h->ny, (n + lbmk::STG_KT - 1) / lbmk::STG_KT);
+    lbmk::stg_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, h->stream>>>(a);
+    h->launches += 1;
+}
+
+// One adjoint step: s_n (FP32 lattice) and lambda_{n+1} -> lambda_n.
+void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lout, const float *utau_n,
+                    const float *vprime_n, float *luin_n, bool seeds, const lbm_objective *obj, float jtau_w) {
+    lbmk::AdjArgs a;
+    const size_t N = (size_t)h->ncell;
+    for (int q = 0; q < 19; ++q) a.in[q] = sn + q * N;
+    a.lam = lam; a.lout = lout; a.outlet = h->adj.outlet;
+    a.utau = utau_n; a.vprime = vprime_n; a.UR = h->d_UR; a.amat = h->d_amat;
+    a.luin = luin_n; a.gtheta = h->adj.gtheta;
+    a.jr_coef = seeds ? h->adj.jr_coef : nullptr;
+    a.jr_mean = h->adj.jr_mean;
+    a.jtau_w = seeds ? jtau_w : 0.0f;
+    a.i_tau0 = obj ? obj->i_tau0 : 0; a.i_tau1 = obj ? obj->i_tau1 : 0; a.i_R = obj ? obj->i_R : -1;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    a.inlet = h->opts.inlet; a.wall_model = h->opts.wall_model;
+    a.tau0 = (float)h->tau0;
+    a.csm18 = (float)(18.0 * std::sqrt(2.0) * h->opts.c_smag);
+    a.y1_nu = (float)(0.5 / h->nu);
+    a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
+    const int bx = 64;
+    dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
+    lbmk::adjoint_kernel<<<grid, block, 0, h->stream>>>(a);
+    h->launches += 1;
+    if (h->opts.inlet) {
+        const int n = h->ny * h->nz;
+        lbmk::adj_outlet_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(lout, h->adj.outlet, h->nx, h->ny, h->nz);
+        h->launches += 1;
+    }
+}
+
+// theta gradient through the inlet velocity for nsteps steps from t0
+void launch_stg_adjoint(lbm_handle *h, long long t0, int nsteps) {
+    if (!h->opts.inlet) return;
+    lbmk::StgAdjArgs a;
+    a.alpha = h->d_alpha; a.betaT = h->d_betaT; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
+    a.sqsig = h->d_sqsig; a.dsq = h->adj.dsq; a.kphase = h->adj.kphase; a.aunit = h->adj.aunit;
+    a.dUR = h->adj.dUR; a.luin = h->adj.luin; a.gtheta = h->adj.gtheta;
+    a.amp = (float)h->theta[1]; a.cell_scale = h->adj.cell_scale;
+    a.t0 = t0; a.nsteps = nsteps; a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
+    dim3 grid((h->nz + lbmk::STG_KZ - 1) / lbmk::STG_KZ, h->ny, (nsteps + lbmk::STG_KT - 1) / lbmk::STG_KT);
+    lbmk::stg_adjoint_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, h->stream>>>(a);
+    h->launches += 1;
 }
 
 template <class S>
@@ -675,7 +906,9 @@ int lbm_set_params(lbm_handle *h, const double theta[4]) {
     for (int c = 0; c < 4; ++c) h->theta[c] = theta[c];
     h->tables();
     if (!h->bound) return LBM_OK;
-    return cuda_fail(h->upload_tables());
+    cudaError_t e = h->upload_tables();
+    if (e == cudaSuccess && h->adj.bound) e = h->upload_adjoint_tables();
+    return cuda_fail(e);
 }
 
 int lbm_set_inlet_profile(lbm_handle *h, const double *U, const double *R) {
@@ -793,8 +1026,206 @@ int lbm_profile_read(lbm_handle *h, double *ms_total, long *step_launches, long 
     return cuda_fail(cudaGetLastError());
 }
 
+int lbm_adjoint_required_bytes(const lbm_handle *h, int window, int ckpt_every, size_t *bytes) {
+    if (!h || !bytes || window < 1 || ckpt_every < 1 || window % ckpt_every) return LBM_EINVAL;
+    Arena ar;
+    lbm_handle *m = const_cast<lbm_handle *>(h);
+    AdjointWork keep = m->adj;
+    *bytes = m->adjoint_layout(ar, window, ckpt_every);
+    m->adj = keep;
+    return LBM_OK;
+}
+
+int lbm_adjoint_bind(lbm_handle *h, int window, int ckpt_every, void *dev_ptr, size_t bytes) {
+    if (!h || window < 1 || ckpt_every < 1 || window % ckpt_every) return LBM_EINVAL;
+    if (h->opts.precision != LBM_FP32) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    size_t need = 0;
+    lbm_adjoint_required_bytes(h, window, ckpt_every, &need);
+    if (h->adj.bound && h->adj.owns && h->adj.mem) cudaFree(h->adj.mem);
+    h->adj = AdjointWork();
+    void *mem = dev_ptr;
+    bool owns = false;
+    if (dev_ptr) {
+        if (((uintptr_t)dev_ptr & 255) != 0) return LBM_EINVAL;
+        if (bytes < need) return LBM_ENOMEM;
+    } else {
+        if (cudaMalloc(&mem, need) != cudaSuccess) { cudaGetLastError(); return LBM_ENOMEM; }
+        owns = true;
+    }
+    Arena ar;
+    ar.base = (char *)mem;
+    h->adjoint_layout(ar, window, ckpt_every);
+    h->adj.mem = mem; h->adj.owns = owns; h->adj.bound = true;
+    h->adj.T = window; h->adj.K = ckpt_every;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(mem, 0, need, h->stream)) != cudaSuccess) return cuda_fail(e);
+    return cuda_fail(h->upload_adjoint_tables());
+}
+
+int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_objective *obj, double *J,
+                     double dJ_dtheta[4]) {
+    if (!h || !obj || !J || !dJ_dtheta) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    if (!h->adj.bound || h->adj.T != window || h->adj.K != ckpt_every) {
+        const int rc = lbm_adjoint_bind(h, window, ckpt_every, nullptr, 0);
+        if (rc) return rc;
+    }
+    if (obj->i_tau0 < 0 || obj->i_tau1 > h->nx || obj->i_tau0 > obj->i_tau1 || obj->i_R < 0 || obj->i_R >= h->nx)
+        return LBM_EINVAL;
+    AdjointWork &A = h->adj;
+    const int T = window, K = ckpt_every, nx = h->nx, ny = h->ny, nz = h->nz;
+    const size_t L = 19 * (size_t)h->ncell, W = 2 * (size_t)nz * nx, I = 3 * (size_t)nz * ny;
+    const long long t0 = h->t;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    // STG field of the window, accumulators
+    if (h->opts.inlet) launch_stg_into(h, A.vwin, t0, T);
+    if ((e = cudaMemsetAsync(A.objacc, 0, (1 + 3 * (size_t)ny) * sizeof(double), st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemsetAsync(A.gtheta, 0, 4 * sizeof(double), st)) != cudaSuccess) return cuda_fail(e);
+    // ---- forward over the window: s_0 copied to checkpoint 0, every K-th state
+    // written straight into its checkpoint, u_tau of step n into uthist[n] ----
+    if ((e = cudaMemcpyAsync(A.ut_init, h->d_utau, W * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(A.ckpt, h->lat[h->cur], L * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    const int obj_blocks = ny + (2 * nz * (obj->i_tau1 - obj->i_tau0) + 127) / 128;
+    const void *cur = A.ckpt;
+    int pp = 0;                                  // next lattice buffer of the ping-pong
+    for (int n = 0; n < T; ++n) {
+        void *out;
+        if ((n + 1) % K == 0 && n + 1 < T) out = A.ckpt + (size_t)((n + 1) / K) * L;
+        else { out = h->lat[pp]; pp ^= 1; }
+        if (out == cur) { out = h->lat[pp]; pp ^= 1; }
+        StepIO io;
+        io.in = cur; io.out = out;
+        io.utau_in = n == 0 ? A.ut_init : A.uthist + (size_t)(n - 1) * W;
+        io.utau = A.uthist + (size_t)n * W;
+        io.fw = h->d_fw; io.vprime = A.vwin + (size_t)n * I; io.stats = false;
+        launch_step_io(h, io);
+        h->t += 1;
+        cur = out;
+        lbmk::objective_kernel<<<obj_blocks, 128, 0, st>>>((const float *)cur, h->d_fw, A.objacc, nx, ny, nz,
+                                                           obj->i_tau0, obj->i_tau1, obj->i_R);
+        h->launches += 1;
+    }
+    h->cur = cur == h->lat[0] ? 0 : 1;          // s_T is in a lattice buffer
+    if ((e = cudaMemcpyAsync(h->d_utau, A.uthist + (size_t)(T - 1) * W, W * 4, cudaMemcpyDeviceToDevice, st)) !=
+        cudaSuccess) return cuda_fail(e);
+    // ---- objective on the host (FP64) and the J_R seeds ----
+    std::vector<double> acc(1 + 3 * (size_t)ny);
+    if ((e = cudaMemcpyAsync(acc.data(), A.objacc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess) return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+    const double ur2 = h->utau_ref * h->utau_ref;
+    const double nw = 2.0 * (obj->i_tau1 - obj->i_tau0) * nz;
+    const double Jt = nw > 0 ? acc[0] / (T * nw * ur2) : 0.0;
+    double JR = 0.0;
+    std::vector<float> coef(ny), mean(2 * (size_t)ny);
+    for (int j = 0; j < ny; ++j) {
+        const double cnt = (double)T * nz;
+        const double mu = acc[1 + 3 * j] / cnt, mv = acc[2 + 3 * j] / cnt, muv = acc[3 + 3 * j] / cnt;
+        const double r = (muv - mu * mv) / ur2 - h->prof_R[6 * (size_t)j + 3] / ur2;
+        JR += r * r;
+        coef[j] = (float)(2.0 * r / (ur2 * cnt));
+        mean[j] = (float)mu;
+        mean[ny + j] = (float)mv;
+    }
+    *J = Jt + JR;
+    if ((e = cudaMemcpyAsync(A.jr_coef, coef.data(), ny * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(A.jr_mean, mean.data(), 2 * ny * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    const float jtau_w = nw > 0 ? (float)(1.0 / (T * nw * ur2)) : 0.0f;
+    // ---- reverse: segments from the last, recompute from the checkpoint ----
+    if ((e = cudaMemsetAsync(A.lamA, 0, L * 4, st)) != cudaSuccess) return cuda_fail(e);
+    float *lam = A.lamA, *lout = A.lamB;
+    const long long t_end = h->t;
+    for (int sgm = T / K - 1; sgm >= 0; --sgm) {
+        const int base = sgm * K;
+        const float *prev = A.ckpt + (size_t)sgm * L;
+        for (int m = 1; m < K; ++m) {
+            const int n = base + m - 1;
+            StepIO io;
+            io.in = prev; io.out = A.seg + (size_t)(m - 1) * L;
+            io.utau_in = n == 0 ? A.ut_init : A.uthist + (size_t)(n - 1) * W;
+            io.utau = A.ut_scr; io.fw = A.fw_scr; io.vprime = A.vwin + (size_t)n * I; io.stats = false;
+            h->t = t0 + n;
+            launch_step_io(h, io);
+            prev = A.seg + (size_t)(m - 1) * L;
+        }
+        for (int n = base + K - 1; n >= base; --n) {
+            const float *sn = n == base ? A.ckpt + (size_t)sgm * L : A.seg + (size_t)(n - base - 1) * L;
+            launch_adjoint(h, sn, lam, lout, A.uthist + (size_t)n * W, A.vwin + (size_t)n * I,
+                           h->opts.inlet ? A.luin + (size_t)n * I : nullptr, true, obj, jtau_w);
+            std::swap(lam, lout);
+        }
+    }
+    h->t = t_end;
+    if (lam != A.lamA) std::swap(A.lamA, A.lamB);   // lambda_0 in lamA
+    launch_stg_adjoint(h, t0, T);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(dJ_dtheta, A.gtheta, 4 * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e);
+    A.have_lambda0 = true;
+    return cuda_fail(cudaStreamSynchronize(st));
+}
+
+int lbm_adjoint_state_gradient(lbm_handle *h, double *lambda0) {
+    if (!h || !lambda0) return LBM_EINVAL;
+    if (!h->adj.bound || !h->adj.have_lambda0) return LBM_ESTATE;
+    const size_t L = 19 * (size_t)h->ncell;
+    std::vector<float> buf(L);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(buf.data(), h->adj.lamA, L * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
+    for (size_t c = 0; c < L; ++c) lambda0[c] = buf[c];
+    return LBM_OK;
+}
+
+int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, double dtheta[4]) {
+    if (!h || !lambda_next || !lambda_prev || !dtheta) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    if (!h->adj.bound) {
+        const int rc = lbm_adjoint_bind(h, 1, 1, nullptr, 0);
+        if (rc) return rc;
+    }
+    AdjointWork &A = h->adj;
+    const size_t L = 19 * (size_t)h->ncell, W = 2 * (size_t)h->nz * h->nx;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    if (h->opts.inlet) launch_stg_into(h, A.vwin, h->t, 1);
+    if ((e = cudaMemsetAsync(A.gtheta, 0, 4 * sizeof(double), st)) != cudaSuccess) return cuda_fail(e);
+    // forward step into scratch for this step's u_tau (the state stays)
+    if ((e = cudaMemcpyAsync(A.ut_scr, h->d_utau, W * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    StepIO io;
+    io.in = h->lat[h->cur]; io.out = A.lamB; io.utau = A.ut_scr; io.fw = A.fw_scr; io.vprime = A.vwin;
+    io.stats = false;
+    launch_step_io(h, io);
+    std::vector<float> buf(L);
+    for (size_t c = 0; c < L; ++c) buf[c] = (float)lambda_next[c];
+    if ((e = cudaMemcpyAsync(A.lamA, buf.data(), L * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    launch_adjoint(h, (const float *)h->lat[h->cur], A.lamA, A.lamB, A.ut_scr, A.vwin,
+                   h->opts.inlet ? A.luin : nullptr, false, nullptr, 0.0f);
+    launch_stg_adjoint(h, h->t, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(buf.data(), A.lamB, L * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(dtheta, A.gtheta, 4 * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+    for (size_t c = 0; c < L; ++c) lambda_prev[c] = buf[c];
+    A.have_lambda0 = false;
+    return LBM_OK;
+}
+
 void lbm_destroy(lbm_handle *h) {
     if (!h) return;
+    if (h->adj.owns && h->adj.mem) { cudaStreamSynchronize(h->stream); cudaFree(h->adj.mem); }
     if (h->bound) cudaStreamSynchronize(h->stream);
     for (size_t c = 0; c < h->ev0.size(); ++c) { cudaEventDestroy(h->ev0[c]); cudaEventDestroy(h->ev1[c]); }
     if (h->owns && h->mem) cudaFree(h->mem);

@@ -306,7 +306,8 @@ struct StepArgs {
     const float *__restrict__ vprime;        // [nz][ny][3] STG field v' of this step (eq:aux_vec)
     const float *__restrict__ UR;            // [ny] inlet mean profile (eq:u_couple)
     const float *__restrict__ amat;          // [ny][6] amp * Cholesky factor (eq:v_fluc)
-    float *__restrict__ utau;                // [2][nz][nx] wall friction velocity
+    const float *utau_in;                    // [2][nz][nx] u_tau warm start (previous step)
+    float *utau;                             // [2][nz][nx] u_tau of this step (may alias utau_in)
     float *__restrict__ fw;                  // [2][nz][nx][3] wall force of this step
     float *__restrict__ ubuf;                // [3][ncell] velocity (statistics steps)
     unsigned *__restrict__ flags;            // [0] Newton failures, [1] divergence
@@ -453,7 +454,8 @@ __device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k
             const float u2x = su2[tx][0], u2z = su2[tx][2];
             // eq:base: tangential part of u_2 (the wall normal is along y), normalized
             const float tn = sqrtf(u2x * u2x + u2z * u2z);
-            float *utp = a.utau + ((size_t)w * nz + k) * nx + i;
+            const size_t iu = ((size_t)w * nz + k) * nx + i;
+            float ut_new = a.utau_in[iu];
             if (tn >= 1e-12f) {
                 const float ex = u2x / tn, ez = u2z / tn;
                 // eq:uhat with the first-cell velocity (no half-force term)
@@ -463,14 +465,15 @@ __device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k
                 float ut = 0.0f;
                 if (ua > 0.0f) {
                     bool ok;
-                    ut = solve_utau_dev(ua, a.y1_nu, a.kappa, a.B, *utp, &ok);
+                    ut = solve_utau_dev(ua, a.y1_nu, a.kappa, a.B, a.utau_in[iu], &ok);
                     if (!ok) atomicAdd(a.flags, 1u);
                 }
-                *utp = ut;
+                ut_new = ut;
                 // tau_w = rho u_tau^2, eq:force_wm with A = 1
                 const float tw = (1.0f + P.drho) * ut * ut * sg;
                 Fx = -tw * ex; Fz = -tw * ez;
             }
+            a.utau[iu] = ut_new;
             float *fwp = a.fw + (((size_t)w * nz + k) * nx + i) * 3;
             fwp[0] = Fx; fwp[1] = Fy; fwp[2] = Fz;
         }
