@@ -226,9 +226,10 @@ __device__ __forceinline__ void reichardt_partials(float yp, float kap, float B,
 // ---------------------------------------------------------------------------
 struct AdjArgs {
     const float *in[19];            // s_n (FP32 f), read by pull
-    const float *__restrict__ lam;  // [19][ncell] dJ/ds_{n+1}
-    float *__restrict__ lout;       // [19][ncell] dJ/ds_n (written by push)
-    float *__restrict__ outlet;     // [5][nz][ny] clamped-outlet adjoints, added by adj_outlet_kernel
+    float *lam;                     // [19][ncell] dJ/ds_{n+1} (its outlet c_x < 0 entries are zeroed
+                                    // once read: the buffer receives atomics in the next adjoint step)
+    float *lout;                    // [19][ncell] dJ/ds_n (written by push; its outlet c_x < 0 entries
+                                    // must be zero on entry)
     const float *__restrict__ utau;  // [2][nz][nx] u_tau of this step (forward result, warm start)
     const float *__restrict__ vprime;  // [nz][ny][3] STG field of this step
     const float *__restrict__ UR;
@@ -358,6 +359,11 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     const int c = G.o00 + G.ic;
 #pragma unroll
     for (int q = 0; q < 19; ++q) lam[q] = valid ? a.lam[q * N + c] : 0.0f;
+    if (a.inlet && valid && i == nx - 1) {
+        // these entries get the atomics of the next (earlier) adjoint step
+#pragma unroll
+        for (int q = 0; q < 19; ++q) if (CX(q) < 0) a.lam[q * N + c] = 0.0f;
+    }
     float lux = 0.f, luy = 0.f;
     if (a.jr_coef && i == a.i_R && valid) {
         // J_R: d/du of the <u'v'> terms, u and v of this collision
@@ -476,17 +482,17 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     }
 
     // ---- push the adjoint back to the pull sources ----
+    // The outlet column's c_x < 0 entries are read twice in the forward step
+    // (by x = nx-2 and, clamped, by x = nx-1): both contributions are added
+    // atomically into entries that start at zero.
     const bool is_outlet = a.inlet && i == nx - 1;
-    int oslot = 0;
+    const bool shares_outlet = a.inlet && i >= nx - 2;
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         if (is_inlet && CX(q) > 0) continue;                       // unknown: not read
-        if (is_outlet && CX(q) < 0) {                              // clamped read: shared target
-            a.outlet[((size_t)oslot * nz + k) * ny + j] = lp[q];
-            ++oslot;
-            continue;
-        }
-        a.lout[(size_t)(WALLBLOCK ? src_plane(q, G) : q) * N + src_off(q, G)] = lp[q];
+        float *dst = a.lout + (size_t)(WALLBLOCK ? src_plane(q, G) : q) * N + src_off(q, G);
+        if (CX(q) < 0 && shares_outlet) atomicAdd(dst, lp[q]);
+        else *dst = lp[q];
     }
     // planes nobody reads: c_x = -1 at x = 0 and c_x = +1 at x = nx-1
     if (is_inlet) {
@@ -511,25 +517,6 @@ __global__ void __launch_bounds__(128, 4) adjoint_kernel(const __grid_constant__
     const int k = blockIdx.z;
     if (blockIdx.y == 0 || blockIdx.y == gridDim.y - 1) adjoint_cell_wall<true>(a, i, j, k, threadIdx.x, sh);
     else adjoint_cell<false>(a, i, j, k, threadIdx.x, sh);
-}
-
-// The clamped outlet reads: the outlet cell's c_x < 0 populations were pulled
-// from the outlet column itself, which the regular pull of x = nx-2 also
-// reads; add their adjoint there.
-__global__ void adj_outlet_kernel(float *lout, const float *outlet, int nx, int ny, int nz) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ny * nz) return;
-    const int j = t % ny, k = t / ny;
-    const long long N = (long long)nx * ny * nz;
-    int slot = 0;
-#pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        if (CX(q) >= 0) continue;
-        int pl, off;
-        pull_source(q, nx - 1, j, k, nx, ny, nz, 1, pl, off);
-        lout[(size_t)pl * N + off] += outlet[((size_t)slot * nz + k) * ny + j];
-        ++slot;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -646,7 +633,7 @@ __global__ void __launch_bounds__(128) objective_kernel(const float *__restrict_
     const int tid = threadIdx.x;
     if ((int)blockIdx.x < ny) {
         const int j = blockIdx.x;
-        double su = 0, sv = 0, suv = 0;
+        float su = 0, sv = 0, suv = 0;
         for (int k = tid; k < nz; k += blockDim.x) {
             const long long c = ((long long)k * ny + j) * nx + iR;
             float r = 0, jx = 0, jy = 0;
@@ -656,7 +643,8 @@ __global__ void __launch_bounds__(128) objective_kernel(const float *__restrict_
                 const float *F = fw + (((size_t)(j == 0 ? 0 : 1) * nz + k) * nx + iR) * 3;
                 jx -= 0.5f * F[0]; jy -= 0.5f * F[1];
             }
-            const double u = jx / r, v = jy / r;
+            const float ir = 1.0f / r;
+            const float u = jx * ir, v = jy * ir;
             su += u; sv += v; suv += u * v;
         }
         red[0][tid] = su; red[1][tid] = sv; red[2][tid] = suv;
@@ -670,7 +658,7 @@ __global__ void __launch_bounds__(128) objective_kernel(const float *__restrict_
     }
     const int w_i = i1 - i0;
     const int e = ((int)blockIdx.x - ny) * blockDim.x + tid;
-    double s = 0.0;
+    float s = 0.0f;
     if (w_i > 0 && e < 2 * nz * w_i) {
         const int ii = i0 + e % w_i, r = e / w_i, k = r % nz, w = r / nz;
         const float *F = fw + (((size_t)w * nz + k) * nx + ii) * 3;

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -78,7 +79,7 @@ struct AdjointWork {
     bool bound = false, owns = false;
     void *mem = nullptr;
     int T = 0, K = 0;
-    float *ckpt = nullptr, *seg = nullptr, *lamA = nullptr, *lamB = nullptr, *outlet = nullptr;
+    float *ckpt = nullptr, *seg = nullptr, *lamA = nullptr, *lamB = nullptr;
     float *ut_init = nullptr, *uthist = nullptr, *ut_scr = nullptr, *fw_scr = nullptr;
     float *vwin = nullptr, *luin = nullptr, *jr_coef = nullptr, *jr_mean = nullptr;
     float *dsq = nullptr, *aunit = nullptr, *dUR = nullptr;
@@ -120,6 +121,7 @@ struct lbm_handle {
     int stg_ring = 1;
     long long stg_t0 = 0, stg_len = 0;
     long long check_every = 16;
+    bool two_cells = true;              // packed two-cell kernel when nx is even
     uint64_t *d_rate64 = nullptr;
     cudaStream_t stream = nullptr;
     long long t = 0;
@@ -348,7 +350,6 @@ struct lbm_handle {
         adj.seg = ar.take<float>(L * (K - 1));
         adj.lamA = ar.take<float>(L);
         adj.lamB = ar.take<float>(L);
-        adj.outlet = ar.take<float>(5 * (size_t)nz * ny);
         adj.ut_init = ar.take<float>(W);
         adj.uthist = ar.take<float>(W * T);
         adj.ut_scr = ar.take<float>(W);
@@ -482,12 +483,20 @@ void launch_step_t(lbm_handle *h, const StepIO &io) {
     a.y1_nu = (float)(0.5 / h->nu);
     a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
     const int bxmax = lbmk::STEP_THREADS / lbmk::BY;
-    const int bx = h->nx >= bxmax ? bxmax : (h->nx >= 64 && bxmax >= 64 ? 64 : 32);
-    dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
     const size_t slot = h->prof_on ? prof_slot(h) : 0;
     if (h->prof_on) cudaEventRecord(h->ev0[slot], h->stream);
-    if (io.stats) lbmk::step_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
-    else lbmk::step_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
+    if (h->nx % 2 == 0 && h->two_cells) {
+        // two cells per thread
+        const int bx = (h->nx / 2) >= bxmax ? bxmax : 32;
+        dim3 block(bx, lbmk::BY), grid((h->nx / 2 + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
+        if (io.stats) lbmk::step2_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
+        else lbmk::step2_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
+    } else {
+        const int bx = h->nx >= bxmax ? bxmax : (h->nx >= 64 && bxmax >= 64 ? 64 : 32);
+        dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
+        if (io.stats) lbmk::step_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
+        else lbmk::step_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
+    }
     if (h->prof_on) cudaEventRecord(h->ev1[slot], h->stream);
     h->launches += 1;
 }
@@ -563,7 +572,7 @@ void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lou
     lbmk::AdjArgs a;
     const size_t N = (size_t)h->ncell;
     for (int q = 0; q < 19; ++q) a.in[q] = sn + q * N;
-    a.lam = lam; a.lout = lout; a.outlet = h->adj.outlet;
+    a.lam = const_cast<float *>(lam); a.lout = lout;
     a.utau = utau_n; a.vprime = vprime_n; a.UR = h->d_UR; a.amat = h->d_amat;
     a.luin = luin_n; a.gtheta = h->adj.gtheta;
     a.jr_coef = seeds ? h->adj.jr_coef : nullptr;
@@ -580,11 +589,6 @@ void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lou
     dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
     lbmk::adjoint_kernel<<<grid, block, 0, h->stream>>>(a);
     h->launches += 1;
-    if (h->opts.inlet) {
-        const int n = h->ny * h->nz;
-        lbmk::adj_outlet_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(lout, h->adj.outlet, h->nx, h->ny, h->nz);
-        h->launches += 1;
-    }
 }
 
 // theta gradient through the inlet velocity for nsteps steps from t0
@@ -665,6 +669,7 @@ int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg, c
                        stg->uniforms ? stg->uniforms + 4 * (size_t)stg->n_modes : nullptr);
     h->theta[0] = stg->ell_e; h->theta[1] = stg->amp; h->theta[2] = opts->kappa; h->theta[3] = opts->B;
     h->opts_kappa0 = opts->kappa;
+    if (const char *v = std::getenv("LBM_GB300_ONE_CELL")) h->two_cells = v[0] == '0';
     h->elem = opts->precision == LBM_FP32 ? 4 : 2;
     h->constants();
     h->tables();
@@ -1140,6 +1145,7 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     const float jtau_w = nw > 0 ? (float)(1.0 / (T * nw * ur2)) : 0.0f;
     // ---- reverse: segments from the last, recompute from the checkpoint ----
     if ((e = cudaMemsetAsync(A.lamA, 0, L * 4, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(A.lamB, 0, L * 4, st)) != cudaSuccess) return cuda_fail(e);
     float *lam = A.lamA, *lout = A.lamB;
     const long long t_end = h->t;
     for (int sgm = T / K - 1; sgm >= 0; --sgm) {
@@ -1209,6 +1215,7 @@ int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, 
     for (size_t c = 0; c < L; ++c) buf[c] = (float)lambda_next[c];
     if ((e = cudaMemcpyAsync(A.lamA, buf.data(), L * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e);
+    if ((e = cudaMemsetAsync(A.lamB, 0, L * 4, st)) != cudaSuccess) return cuda_fail(e);
     launch_adjoint(h, (const float *)h->lat[h->cur], A.lamA, A.lamB, A.ut_scr, A.vwin,
                    h->opts.inlet ? A.luin : nullptr, false, nullptr, 0.0f);
     launch_stg_adjoint(h, h->t, 1);

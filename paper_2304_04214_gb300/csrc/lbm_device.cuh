@@ -45,23 +45,38 @@ constexpr float S_M = 1.98f;     // moments 16, 17, 18
 // hold the deviation f - w_q.  SHIFTED tells the collision which of the two
 // its registers hold (the arithmetic is FP32 either way).
 // ---------------------------------------------------------------------------
+// ld2 / st2 move two adjacent populations (even offset) in one access.
 struct StoreF32 {
     using T = float;
     static constexpr bool SHIFTED = false;
     static __device__ __forceinline__ float ld(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    static __device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 };
 struct StoreF16 {
     using T = __half;
     static constexpr bool SHIFTED = true;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float2 ld2(const __half *p) {
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    }
+    static __device__ __forceinline__ void st2(__half *p, float2 v) {
+        *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v);
+    }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
     static constexpr bool SHIFTED = true;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    }
+    static __device__ __forceinline__ void st2(__nv_bfloat16 *p, float2 v) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
+    }
 };
 
 // Approximate reciprocal and square root (PTX rcp/sqrt.approx, about one ulp);
@@ -274,6 +289,114 @@ __device__ __forceinline__ void collide_mrt(float (&f)[19], const Pairs &P, floa
 }
 
 // ---------------------------------------------------------------------------
+// Two cells per thread: packed FP32x2 arithmetic (sm_100 family) so that one
+// instruction updates both cells.  V2 holds (cell i, cell i+1).
+// ---------------------------------------------------------------------------
+typedef float2 V2;
+__device__ __forceinline__ V2 vdup(float s) { return make_float2(s, s); }
+__device__ __forceinline__ V2 operator+(V2 a, V2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return __ffma2_rn(b, vdup(-1.0f), a); }
+__device__ __forceinline__ V2 operator-(V2 a) { return __fmul2_rn(a, vdup(-1.0f)); }
+__device__ __forceinline__ V2 operator*(V2 a, V2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ V2 operator*(float s, V2 b) { return __fmul2_rn(vdup(s), b); }
+__device__ __forceinline__ V2 operator*(V2 b, float s) { return __fmul2_rn(b, vdup(s)); }
+__device__ __forceinline__ V2 vfma(V2 a, V2 b, V2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ V2 vfma(float a, V2 b, V2 c) { return __ffma2_rn(vdup(a), b, c); }
+__device__ __forceinline__ V2 vrcp(V2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+__device__ __forceinline__ V2 vsqrt(V2 a) { return make_float2(sqrt_approx(a.x), sqrt_approx(a.y)); }
+
+// Force-free MRT-LES collision of two cells (interior rows): the same
+// algebra as collide_mrt<SHIFTED, false>, written with fused packed operations.
+template <bool SHIFTED>
+__device__ __forceinline__ void collide_mrt2(V2 (&f)[19], float tau0, float csm18, V2 &ux_o, V2 &uy_o,
+                                             V2 &uz_o) {
+    V2 s[9], d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) { s[p] = f[p] + f[18 - p]; d[p] = f[p] - f[18 - p]; }
+    const V2 f9 = f[9];
+    const V2 s04 = s[0] + s[4], s13 = s[1] + s[3], s57 = s[5] + s[7], s26 = s[2] + s[6];
+    const V2 Sdg = (s04 + s13) + s57;
+    const V2 Sax = s26 + s[8];
+    // rho and momentum (eq:density, eq:momentum)
+    const V2 rho = SHIFTED ? (Sdg + Sax) + f9 + vdup(1.0f) : (Sdg + Sax) + f9;
+    const V2 Dx = (d[3] - d[1]) + (d[7] - d[5]);
+    const V2 Dy = (d[4] - d[0]) - (d[5] + d[7]);
+    const V2 Dz = -(d[0] + d[4]) - (d[1] + d[3]);
+    const V2 jx = Dx - d[8], jy = Dy - d[6], jz = Dz - d[2];
+    const V2 irho = vrcp(rho);
+    const V2 ux = jx * irho, uy = jy * irho, uz = jz * irho;
+    ux_o = ux; uy_o = uy; uz_o = uz;
+    const V2 uxx = jx * ux, uyy = jy * uy, uzz = jz * uz;
+    const V2 uxy = jx * uy, uyz = jy * uz, uxz = jx * uz;
+    const V2 usq = (uxx + uyy) + uzz;
+    // non-equilibrium moments; M w = (1, -11, 3, 0, ...) sets the constants
+    const V2 e1 = vfma(-30.0f, f9, vfma(8.0f, Sdg, -11.0f * Sax));
+    const V2 e2 = vfma(12.0f, f9, vfma(-4.0f, Sax, Sdg));
+    const V2 r11 = SHIFTED ? 11.0f * (rho - vdup(1.0f)) : 11.0f * rho;
+    const V2 r3 = SHIFTED ? -3.0f * (rho - vdup(1.0f)) : -3.0f * rho;
+    const V2 n1 = vfma(-19.0f, usq, e1 + r11);
+    const V2 n2 = vfma(5.5f, usq, e2 + r3);
+    const V2 n4 = vfma(5.0f, d[8], vfma(2.0f / 3.0f, jx, jx));
+    const V2 n6 = vfma(5.0f, d[6], vfma(2.0f / 3.0f, jy, jy));
+    const V2 n8 = vfma(5.0f, d[2], vfma(2.0f / 3.0f, jz, jz));
+    const V2 pxx_eq = vfma(2.0f, uxx, -(uyy + uzz));
+    const V2 pww_eq = uyy - uzz;
+    const V2 t1357 = s13 + s57;
+    const V2 n9 = vfma(2.0f, s[8] - s04, t1357 - s26) - pxx_eq;
+    const V2 n10 = vfma(-4.0f, s[8], vfma(2.0f, s26 - s04, t1357)) + 0.5f * pxx_eq;
+    const V2 d57m13 = s57 - s13;
+    const V2 n11 = (s[6] - s[2]) + d57m13 - pww_eq;
+    const V2 n12 = vfma(2.0f, s[2] - s[6], d57m13) + 0.5f * pww_eq;
+    const V2 n13 = (s[5] - s[7]) - uxy;
+    const V2 n14 = (s[0] - s[4]) - uyz;
+    const V2 n15 = (s[1] - s[3]) - uxz;
+    const V2 n16 = (d[1] - d[3]) + (d[7] - d[5]);
+    const V2 n17 = (d[4] - d[0]) + (d[5] + d[7]);
+    const V2 n18 = (d[0] + d[4]) - (d[1] + d[3]);
+    // Pi_neq and the Smagorinsky rate (eq:tau_eff)
+    const V2 c2 = n1 * (1.0f / 57.0f);                 // (n1 / 19) / 3
+    const V2 pxx = vfma(1.0f / 3.0f, n9, c2);
+    const V2 pyz_common = vfma(-1.0f / 6.0f, n9, c2);
+    const V2 pyy = vfma(0.5f, n11, pyz_common);
+    const V2 pzz = vfma(-0.5f, n11, pyz_common);
+    V2 qq = vfma(pxx, pxx, vfma(pyy, pyy, pzz * pzz));
+    qq = vfma(2.0f * n13, n13, vfma(2.0f * n14, n14, vfma(2.0f * n15, n15, qq)));
+    const V2 tt = vdup(tau0);
+    const V2 sv = 2.0f * vrcp(tt + vsqrt(vfma(csm18 * vsqrt(qq), irho, tt * tt)));
+    // relaxation: G_k = s_k n_k / |row_k|^2
+    const V2 G1 = n1 * (S_E / 2394.0f), G2 = n2 * (S_EPS / 252.0f);
+    const V2 G4 = n4 * (S_Q / 40.0f), G6 = n6 * (S_Q / 40.0f), G8 = n8 * (S_Q / 40.0f);
+    const V2 sv36 = sv * (1.0f / 36.0f), sv12 = sv * (1.0f / 12.0f), sv4 = sv * 0.25f;
+    const V2 G9 = sv36 * n9, G10 = n10 * (S_PI / 72.0f);
+    const V2 G11 = sv12 * n11, G12 = n12 * (S_PI / 24.0f);
+    const V2 G13 = sv4 * n13, G14 = sv4 * n14, G15 = sv4 * n15;
+    const V2 G16 = n16 * (S_M * 0.125f), G17 = n17 * (S_M * 0.125f), G18 = n18 * (S_M * 0.125f);
+    // f* = f - M^T g by opposite pairs (no force: G3 = G5 = G7 = 0), rebuilt
+    // from the pair sums: f*_p = (s_p/2 - E) + (d_p/2 - O), f*_{18-p} = (s_p/2 - E) - (d_p/2 - O)
+    const V2 Aax = vfma(-11.0f, G1, -4.0f * G2);
+    const V2 Ddg = vfma(8.0f, G1, G2);
+    const V2 g9_10 = G9 + G10, g11_12 = G11 + G12;
+    const V2 Xa = vfma(-2.0f, g9_10, Ddg);            // pairs 0, 4
+    const V2 Xb = (Ddg + g9_10) - g11_12;             // pairs 1, 3
+    const V2 Xc = (Ddg + g9_10) + g11_12;             // pairs 5, 7
+    auto put = [&](int p, V2 E, V2 O) {
+        const V2 hs = vfma(0.5f, s[p], -E), hd = vfma(0.5f, d[p], -O);
+        f[p] = hs + hd;
+        f[18 - p] = hs - hd;
+    };
+    put(0, Xa + G14, (G18 - G17) - (G6 + G8));
+    put(1, Xb + G15, (G16 - G18) - (G4 + G8));
+    put(2, vfma(2.0f, G10 + G12, Aax - (G9 + G11)), 4.0f * G8);
+    put(3, Xb - G15, (G4 - G8) - (G16 + G18));
+    put(4, Xa - G14, (G6 - G8) + (G17 + G18));
+    put(5, Xc + G13, (G17 - G16) - (G4 + G6));
+    put(6, vfma(2.0f, G10 - G12, (Aax - G9) + G11), 4.0f * G6);
+    put(7, Xc - G13, (G4 - G6) + (G16 + G17));
+    put(8, vfma(2.0f, G9, vfma(-4.0f, G10, Aax)), 4.0f * G4);
+    f[9] = vfma(30.0f, G1, vfma(-12.0f, G2, f9));
+}
+
+// ---------------------------------------------------------------------------
 // Pull source of population q for cell (i, j, k) under the boundary rules:
 // z periodic; x clamped (inlet on: the inlet rebuilds c_x > 0, the outlet
 // copy is the clamp at nx-1) or periodic; specular slip walls mirror c_y and
@@ -431,7 +554,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<S> &a, const float (&
 template <class S, bool STATS>
 __device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k, int tx, int o00, int ozm,
                                        int ozp, int ic, int xm, int xp) {
-    __shared__ float su2[STEP_THREADS / BY][3];
+    __shared__ float su2[2 * STEP_THREADS / BY][3];   // slot tx (one or two per thread)
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const bool bot = j == 0, top = j == ny - 1;
     const bool valid = i < nx;
@@ -519,6 +642,91 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, LBM_STEP_MINB) step_kernel(c
     float ux, uy, uz;
     collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, a.tau0, a.csm18, ux, uy, uz);
     if (i < nx) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
+}
+
+// Two x-adjacent cells (i, i+1), i even, per thread: vector loads for the
+// populations with c_x = 0, two scalar loads for the shifted ones, packed FP32x2
+// arithmetic, vector stores.  nx must be even.  The first and last block rows
+// run the scalar wall path once per cell.
+// Resident blocks per SM the register budget aims for: FP32 storage is bound
+// by memory latency at five, the 16-bit formats move half the bytes and gain
+// from the sixth block's extra warps.
+#ifndef LBM_STEP2_MINB32
+#define LBM_STEP2_MINB32 5
+#endif
+#ifndef LBM_STEP2_MINB16
+#define LBM_STEP2_MINB16 6
+#endif
+template <class S> struct Step2Blocks { static constexpr int value = LBM_STEP2_MINB16; };
+template <> struct Step2Blocks<StoreF32> { static constexpr int value = LBM_STEP2_MINB32; };
+
+template <class S, bool STATS>
+__global__ void __launch_bounds__(LBM_STEP_THREADS, Step2Blocks<S>::value) step2_kernel(const __grid_constant__ StepArgs<S> a) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int bxi = a.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int byi = a.reverse ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+    const int i0 = 2 * (bxi * blockDim.x + tx);
+    const int j = byi * BY + ty;
+    const int k = a.reverse ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    const int plane = nx * ny;
+    const int ozm = k == 0 ? (nz - 1) * plane : -plane;      // source plane for c_z = +1
+    const int ozp = k == nz - 1 ? -(nz - 1) * plane : plane;  // source plane for c_z = -1
+    const int o00 = (k * ny + j) * nx;
+
+    if (byi == 0 || byi == gridDim.y - 1) {               // block-uniform: scalar wall path per cell
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + h;
+            const int ic = i < nx ? i : nx - 1;
+            int xm = ic - 1, xp = ic + 1;
+            if (a.inlet) { xm = max(xm, 0); xp = min(xp, nx - 1); }
+            else { xm = xm < 0 ? nx - 1 : xm; xp = xp >= nx ? 0 : xp; }
+            wall_rows<S, STATS>(a, i, j, k, tx + h * blockDim.x, o00, ozm, ozp, ic, xm, xp);
+        }
+        return;
+    }
+    const bool valid = i0 < nx;
+    const int ic = valid ? i0 : nx - 2;
+    int xm0 = ic - 1, xp1 = ic + 2;                  // lo cell's c_x=+1 source, hi cell's c_x=-1 source
+    if (a.inlet) { xm0 = max(xm0, 0); xp1 = min(xp1, nx - 1); }
+    else { xm0 = xm0 < 0 ? nx - 1 : xm0; xp1 = xp1 >= nx ? 0 : xp1; }
+    const int rm = o00 - nx, rp = o00 + nx;          // rows for c_y = +1 / -1
+    V2 f[19];
+#define LD_C0(q, row) f[q] = S::ld2(a.in[q] + (row) + ic)
+#define LD_CP(q, row) f[q] = make_float2(S::ld(a.in[q] + (row) + xm0), S::ld(a.in[q] + (row) + ic))
+#define LD_CM(q, row) f[q] = make_float2(S::ld(a.in[q] + (row) + ic + 1), S::ld(a.in[q] + (row) + xp1))
+    LD_C0(0, rp + ozp); LD_CM(1, o00 + ozp); LD_C0(2, o00 + ozp); LD_CP(3, o00 + ozp); LD_C0(4, rm + ozp);
+    LD_CM(5, rp);       LD_C0(6, rp);        LD_CP(7, rp);        LD_CM(8, o00);       LD_C0(9, o00);
+    LD_CP(10, o00);     LD_CM(11, rm);       LD_C0(12, rm);       LD_CP(13, rm);       LD_C0(14, rp + ozm);
+    LD_CM(15, o00 + ozm); LD_C0(16, o00 + ozm); LD_CP(17, o00 + ozm); LD_C0(18, rm + ozm);
+#undef LD_C0
+#undef LD_CP
+#undef LD_CM
+    if (a.inlet && i0 == 0) {                        // the lo cell is an inlet cell
+        float fl[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) fl[q] = f[q].x;
+        inlet_rebuild<S>(a, fl, j, k);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q].x = fl[q];
+    }
+    V2 ux, uy, uz;
+    collide_mrt2<S::SHIFTED>(f, a.tau0, a.csm18, ux, uy, uz);
+    if (!valid) return;
+    const int c = o00 + ic;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) S::st2(a.out[q] + c, f[q]);
+    if (STATS) {
+        const long long N = (long long)plane * nz;
+        *reinterpret_cast<float2 *>(a.ubuf + c) = ux;
+        *reinterpret_cast<float2 *>(a.ubuf + N + c) = uy;
+        *reinterpret_cast<float2 *>(a.ubuf + 2 * N + c) = uz;
+    }
+    if (a.check) {
+        const V2 uu = vfma(ux, ux, vfma(uy, uy, uz * uz));
+        if (!(uu.x < 0.09f) || !(uu.y < 0.09f)) atomicAdd(a.flags + 1, 1u);   // also catches NaN
+    }
 }
 
 // ---------------------------------------------------------------------------
