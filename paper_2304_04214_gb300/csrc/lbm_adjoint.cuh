@@ -37,7 +37,7 @@ __device__ __forceinline__ void collide_adjoint(const float (&lam)[19], const Pa
                                                 float luz, AdjIn &A) {
     const float *s = P.s;
     // ---------------- forward values ----------------
-    const float rho = 1.0f + P.drho, irho = 1.0f / rho;
+    const float rho = 1.0f + P.drho, irho = rcp_approx(rho);
     const float rux = P.jx + 0.5f * Fx, ruy = P.jy + 0.5f * Fy, ruz = P.jz + 0.5f * Fz;
     const float ux = rux * irho, uy = ruy * irho, uz = ruz * irho;
     const float uxx = rux * ux, uyy = ruy * uy, uzz = ruz * uz;
@@ -57,9 +57,9 @@ __device__ __forceinline__ void collide_adjoint(const float (&lam)[19], const Pa
     const float pyy = (c2 - 0.5f * n9 + 1.5f * n11) * (1.0f / 3.0f);
     const float pzz = (c2 - 0.5f * n9 - 1.5f * n11) * (1.0f / 3.0f);
     const float qq = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (n13 * n13 + n14 * n14 + n15 * n15);
-    const float Qh = sqrtf(qq);
-    const float Rr = sqrtf(tau0 * tau0 + csm18 * Qh * irho);
-    const float sv = 2.0f / (tau0 + Rr);
+    const float Qh = sqrt_approx(qq);
+    const float Rr = sqrt_approx(tau0 * tau0 + csm18 * Qh * irho);
+    const float sv = 2.0f * rcp_approx(tau0 + Rr);
     const float hv = 1.0f - 0.5f * sv;
     float F9 = 0.f, F11 = 0.f, F13 = 0.f, F14 = 0.f, F15 = 0.f;
     if (HAS_FORCE) {
@@ -93,28 +93,28 @@ __device__ __forceinline__ void collide_adjoint(const float (&lam)[19], const Pa
     const float m18 = (ld[0] + ld[4]) - (ld[1] + ld[3]);
     // L = lambda . f* = lambda . f - sum_k mu_k G_k  ->  a_k = dL/dG_k = -mu_k
     // ---------------- reverse through G ----------------
-    float bn1 = -m1 * S_E / 2394.0f;
-    float bn2 = -m2 * S_EPS / 252.0f;
-    const float bn4 = -m4 * S_Q / 40.0f, bn6 = -m6 * S_Q / 40.0f, bn8 = -m8 * S_Q / 40.0f;
-    float bn9 = -m9 * sv / 36.0f;
-    const float bn10 = -m10 * S_PI / 72.0f;
-    float bn11 = -m11 * sv / 12.0f;
-    const float bn12 = -m12 * S_PI / 24.0f;
+    float bn1 = -m1 * (S_E / 2394.0f);
+    float bn2 = -m2 * (S_EPS / 252.0f);
+    const float bn4 = -m4 * (S_Q / 40.0f), bn6 = -m6 * (S_Q / 40.0f), bn8 = -m8 * (S_Q / 40.0f);
+    float bn9 = -m9 * sv * (1.0f / 36.0f);
+    const float bn10 = -m10 * (S_PI / 72.0f);
+    float bn11 = -m11 * sv * (1.0f / 12.0f);
+    const float bn12 = -m12 * (S_PI / 24.0f);
     float bn13 = -m13 * sv * 0.25f, bn14 = -m14 * sv * 0.25f, bn15 = -m15 * sv * 0.25f;
     const float bn16 = -m16 * S_M * 0.125f, bn17 = -m17 * S_M * 0.125f, bn18 = -m18 * S_M * 0.125f;
     // d/dsv of (sv n - (1 - sv/2) F) = n + F/2
-    float bsv = -m9 * (n9 + 0.5f * F9) / 36.0f - m11 * (n11 + 0.5f * F11) / 12.0f
+    float bsv = -m9 * (n9 + 0.5f * F9) * (1.0f / 36.0f) - m11 * (n11 + 0.5f * F11) * (1.0f / 12.0f)
               - (m13 * (n13 + 0.5f * F13) + m14 * (n14 + 0.5f * F14) + m15 * (n15 + 0.5f * F15)) * 0.25f;
     float lFx = 0.f, lFy = 0.f, lFz = 0.f;
     float lux_ = lux, luy_ = luy, luz_ = luz;
     if (HAS_FORCE) {
         const float cq = (1.0f - 0.5f * S_Q) * (2.0f / 3.0f);
-        const float buF = m1 * (1.0f - 0.5f * S_E) * 38.0f / 2394.0f - m2 * (1.0f - 0.5f * S_EPS) * 11.0f / 252.0f;
-        lFx += 0.1f * m3 - m4 * cq / 40.0f;
-        lFy += 0.1f * m5 - m6 * cq / 40.0f;
-        lFz += 0.1f * m7 - m8 * cq / 40.0f;
-        const float bF9 = m9 * hv / 36.0f - m10 * (1.0f - 0.5f * S_PI) * 0.5f / 72.0f;
-        const float bF11 = m11 * hv / 12.0f - m12 * (1.0f - 0.5f * S_PI) * 0.5f / 24.0f;
+        const float buF = m1 * ((1.0f - 0.5f * S_E) * 38.0f / 2394.0f) - m2 * ((1.0f - 0.5f * S_EPS) * 11.0f / 252.0f);
+        lFx += 0.1f * m3 - m4 * (cq * (1.0f / 40.0f));
+        lFy += 0.1f * m5 - m6 * (cq * (1.0f / 40.0f));
+        lFz += 0.1f * m7 - m8 * (cq * (1.0f / 40.0f));
+        const float bF9 = m9 * hv * (1.0f / 36.0f) - m10 * ((1.0f - 0.5f * S_PI) * 0.5f / 72.0f);
+        const float bF11 = m11 * hv * (1.0f / 12.0f) - m12 * ((1.0f - 0.5f * S_PI) * 0.5f / 24.0f);
         const float bF13 = m13 * hv * 0.25f, bF14 = m14 * hv * 0.25f, bF15 = m15 * hv * 0.25f;
         // uF = u . F
         lux_ += buF * Fx; luy_ += buF * Fy; luz_ += buF * Fz;
@@ -135,10 +135,10 @@ __device__ __forceinline__ void collide_adjoint(const float (&lam)[19], const Pa
     float lirho = 0.f;
     {
         const float lR = bsv * (-0.5f * sv * sv);
-        const float lX = lR * 0.5f / Rr;
+        const float lX = lR * 0.5f * rcp_approx(Rr);
         const float lQh = lX * csm18 * irho;
         lirho += lX * csm18 * Qh;
-        const float lqq = Qh > 1e-30f ? lQh * 0.5f / Qh : 0.0f;
+        const float lqq = Qh > 1e-30f ? lQh * 0.5f * rcp_approx(Qh) : 0.0f;
         const float lpxx = 2.0f * pxx * lqq, lpyy = 2.0f * pyy * lqq, lpzz = 2.0f * pzz * lqq;
         bn13 += 4.0f * n13 * lqq; bn14 += 4.0f * n14 * lqq; bn15 += 4.0f * n15 * lqq;
         const float lc2 = (lpxx + lpyy + lpzz) * (1.0f / 3.0f);
@@ -217,9 +217,9 @@ __device__ __forceinline__ void reichardt_partials(float yp, float kap, float B,
                                                    float &dB) {
     const float e11 = expf(-yp * (1.0f / 11.0f)), e3 = expf(-yp * (1.0f / 3.0f));
     const float l1 = log1pf(kap * yp);
-    up = l1 / kap + B * (1.0f - e11 - yp * (1.0f / 11.0f) * e3);
-    dup = 1.0f / (1.0f + kap * yp) + B * (e11 * (1.0f / 11.0f) - e3 * (1.0f / 11.0f) + yp * (1.0f / 33.0f) * e3);
-    dk = -l1 / (kap * kap) + yp / (kap * (1.0f + kap * yp));
+    up = l1 * (1.0f / kap) + B * (1.0f - e11 - yp * (1.0f / 11.0f) * e3);
+    dup = rcp_approx(1.0f + kap * yp) + B * (e11 * (1.0f / 11.0f) - e3 * (1.0f / 11.0f) + yp * (1.0f / 33.0f) * e3);
+    dk = (-l1 + kap * yp * rcp_approx(1.0f + kap * yp)) * rcp_approx(kap * kap);
     dB = 1.0f - e11 - yp * (1.0f / 11.0f) * e3;
 }
 
@@ -296,7 +296,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
         for (int q = 0; q < 19; ++q) f[q] -= WQ(q);
         const float sk = (f[0] + f[2] + f[4] + f[6] + f[9] + f[12] + f[14] + f[16] + f[18])
                        + 2.0f * (f[1] + f[5] + f[8] + f[11] + f[15]);
-        rin = (1.0f + sk) / (1.0f - vx);
+        rin = (1.0f + sk) * rcp_approx(1.0f - vx);
         const float drin = rin - 1.0f, vv = vx * vx + vy * vy + vz * vz;
         auto feq = [&](int q) {
             const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
@@ -331,15 +331,16 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     float ex = 0.f, ez = 0.f, tn = 0.f, ut = 0.f, sg = 1.f, irho_w = 0.f;
     float irho2 = 0.f, j2x = 0.f, j2z = 0.f;
     if (WALLBLOCK && a.wall_model) {
-        if (!(bot || top)) { sh[tx][0] = P.jx; sh[tx][1] = P.jz; sh[tx][2] = 1.0f / (1.0f + P.drho); }
+        if (!(bot || top)) { sh[tx][0] = P.jx; sh[tx][1] = P.jz; sh[tx][2] = rcp_approx(1.0f + P.drho); }
         __syncthreads();
         if (is_wall) {
             j2x = sh[tx][0]; j2z = sh[tx][1]; irho2 = sh[tx][2];
             const float u2x = j2x * irho2, u2z = j2z * irho2;
-            irho_w = 1.0f / (1.0f + P.drho);
-            tn = sqrtf(u2x * u2x + u2z * u2z);
+            irho_w = rcp_approx(1.0f + P.drho);
+            tn = sqrt_approx(u2x * u2x + u2z * u2z);
             if (tn >= 1e-12f) {
-                ex = u2x / tn; ez = u2z / tn;
+                const float itn = rcp_approx(tn);
+                ex = u2x * itn; ez = u2z * itn;
                 const float uhat = (P.jx * ex + P.jz * ez) * irho_w;
                 sg = uhat < 0.0f ? -1.0f : 1.0f;
                 const float ua = fabsf(uhat);
@@ -368,7 +369,8 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     if (a.jr_coef && i == a.i_R && valid) {
         // J_R: d/du of the <u'v'> terms, u and v of this collision
         const float rho = 1.0f + P.drho;
-        const float uu = (P.jx + 0.5f * Fx) / rho, vv = P.jy / rho;
+        const float ir = rcp_approx(rho);
+        const float uu = (P.jx + 0.5f * Fx) * ir, vv = P.jy * ir;
         const float cj = a.jr_coef[j];
         lux = cj * (vv - a.jr_mean[ny + j]);
         luy = cj * (uu - a.jr_mean[j]);
@@ -394,9 +396,10 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
                 const float yp = a.y1_nu * ut;
                 reichardt_partials(yp, a.kappa, a.B, up, dup, dk, dB);
                 const float Ru = up + yp * dup;
-                const float lua = lut / Ru;
-                gk = -lut * ut * dk / Ru;
-                gB = -lut * ut * dB / Ru;
+                const float iRu = rcp_approx(Ru);
+                const float lua = lut * iRu;
+                gk = -lut * ut * dk * iRu;
+                gB = -lut * ut * dB * iRu;
                 const float luh = sg * lua;
                 // uhat = (jx ex + jz ez) irho_w
                 A.ljx += ex * irho_w * luh; A.ljz += ez * irho_w * luh;
@@ -406,7 +409,8 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
             }
             // e = t / |t|, t = (u2x, u2z)
             const float dot = lex * ex + lez * ez;
-            const float lu2x = (lex - dot * ex) / tn, lu2z = (lez - dot * ez) / tn;
+            const float itn = rcp_approx(tn);
+            const float lu2x = (lex - dot * ex) * itn, lu2z = (lez - dot * ez) * itn;
             // u2 = j2 irho2
             lj2x = irho2 * lu2x; lj2z = irho2 * lu2z;
             lirho2 = j2x * lu2x + j2z * lu2z;
@@ -415,7 +419,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
         __syncthreads();
         if (!(bot || top)) {
             const float li2 = sh[tx][2];
-            const float ir = 1.0f / (1.0f + P.drho);
+            const float ir = rcp_approx(1.0f + P.drho);
             A.ljx += sh[tx][0]; A.ljz += sh[tx][1];
             A.lrho += -ir * ir * li2;
         }
@@ -470,8 +474,9 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
         (void)drin;
         lvx += 2.0f * vx * lvv; lvy += 2.0f * vy * lvv; lvz += 2.0f * vz * lvv;
         // rin = (1 + sk) / (1 - vx), sk = sum_{c_x=0} fin + 2 sum_{c_x<0} fin
-        const float lsk = lrin / (1.0f - vx);
-        lvx += lrin * rin / (1.0f - vx);
+        const float ivx = rcp_approx(1.0f - vx);
+        const float lsk = lrin * ivx;
+        lvx += lrin * rin * ivx;
 #pragma unroll
         for (int q = 0; q < 19; ++q)
             lp[q] = CX(q) > 0 ? 0.0f : f[q] + (CX(q) == 0 ? lsk : 2.0f * lsk);
@@ -484,20 +489,30 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     // ---- push the adjoint back to the pull sources ----
     // The outlet column's c_x < 0 entries are read twice in the forward step
     // (by x = nx-2 and, clamped, by x = nx-1): both contributions are added
-    // atomically into entries that start at zero.
+    // atomically into entries that start at zero.  Unknown inlet populations
+    // were not read.  The planes nobody reads (c_x = -1 at x = 0, c_x = +1 at
+    // x = nx-1) get zeros.
+    auto dst = [&](int q) { return a.lout + (size_t)(WALLBLOCK ? src_plane(q, G) : q) * N + src_off(q, G); };
     const bool is_outlet = a.inlet && i == nx - 1;
     const bool shares_outlet = a.inlet && i >= nx - 2;
+    if (!is_inlet && !shares_outlet) {
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        if (is_inlet && CX(q) > 0) continue;                       // unknown: not read
-        float *dst = a.lout + (size_t)(WALLBLOCK ? src_plane(q, G) : q) * N + src_off(q, G);
-        if (CX(q) < 0 && shares_outlet) atomicAdd(dst, lp[q]);
-        else *dst = lp[q];
-    }
-    // planes nobody reads: c_x = -1 at x = 0 and c_x = +1 at x = nx-1
-    if (is_inlet) {
+        for (int q = 0; q < 19; ++q) *dst(q) = lp[q];
+    } else if (is_inlet) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            if (CX(q) > 0) continue;
+            if (CX(q) < 0 && shares_outlet) atomicAdd(dst(q), lp[q]);
+            else *dst(q) = lp[q];
+        }
 #pragma unroll
         for (int q = 0; q < 19; ++q) if (CX(q) < 0) a.lout[(size_t)q * N + c] = 0.0f;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            if (CX(q) < 0) atomicAdd(dst(q), lp[q]);
+            else *dst(q) = lp[q];
+        }
     }
     if (is_outlet) {
 #pragma unroll
@@ -643,7 +658,7 @@ __global__ void __launch_bounds__(128) objective_kernel(const float *__restrict_
                 const float *F = fw + (((size_t)(j == 0 ? 0 : 1) * nz + k) * nx + iR) * 3;
                 jx -= 0.5f * F[0]; jy -= 0.5f * F[1];
             }
-            const float ir = 1.0f / r;
+            const float ir = rcp_approx(r);
             const float u = jx * ir, v = jy * ir;
             su += u; sv += v; suv += u * v;
         }
