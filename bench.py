@@ -59,13 +59,18 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lbm_device.cuh", "lbm_api.cu"):
+    for f in ("lbm_device.cuh", "lbm_staged.cuh", "lbm_api.cu"):
         with open(os.path.join(ROOT, "paper_2304_04214_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(cfg_key, precision, ncell):
+KERNEL_NAMES = {"cell": "lbmk::step_kernel", "pair": "lbmk::step2_kernel + lbmk::wall_kernel",
+                "quad": "lbmk::step4_kernel + lbmk::wall_kernel",
+                "staged": "lbmk::staged_kernel + lbmk::wall_kernel"}
+
+
+def recorded_traffic(cfg_key, precision, kernel, ncell):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     or None when the summary is for another build of the kernel."""
     try:
@@ -75,7 +80,7 @@ def recorded_traffic(cfg_key, precision, ncell):
         return None
     if rec.get("source_hash") != kernel_source_hash():
         return None
-    ent = rec.get("entries", {}).get(f"{cfg_key}_{precision}")
+    ent = rec.get("entries", {}).get(f"{cfg_key}_{precision}_{kernel}")
     if not ent:
         return None
     return ent["bytes_per_cell"] * ncell
@@ -222,8 +227,9 @@ def run_native(args, cfg, ws, rank, local):
     ncell = nx * ny * nz
     ch = LBMChannel(nx, ny, nz, re_tau=cfg["re_tau"], n_modes=cfg["n_modes"],
                     seed=cfg["seed"] + 1000 * rank, precision=args.precision,
-                    stats_every=STATS_EVERY, device=dev)
+                    stats_every=STATS_EVERY, step_kernel=args.kernel, device=dev)
     lib, h = ch.lib, ch.h
+    kernel = ch.step_kernel
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -263,7 +269,7 @@ def run_native(args, cfg, ws, rank, local):
     kern_ms = ms_k.value / max(nk.value, 1)
     alg_bytes = BYTES_PER_CELL[args.precision] * ncell
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(args.config, args.precision, ncell)
+    traffic = recorded_traffic(args.config, args.precision, kernel, ncell)
 
     # ---- end to end through the C ABI with host buffers ----
     # each step: the RANS-side inlet profile (U, R) from pinned host memory,
@@ -321,7 +327,7 @@ def run_native(args, cfg, ws, rank, local):
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(achieved / peaks["hbm_gbs"], 4),
                          "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": "lbmk::step_kernel", "kernel_ms": round(kern_ms, 5),
+                         "kernel": KERNEL_NAMES[kernel], "kernel_ms": round(kern_ms, 5),
                          "algorithmic_bytes": alg_bytes},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e, 1), "unit": "MLUPS",
@@ -381,6 +387,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "quad", "staged"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -48,6 +48,7 @@ extern "C" {
 #define LBM_ENOTCONV   -5   /* the u_tau Newton solve did not converge */
 #define LBM_ESTATE     -6   /* call out of order (e.g. step before memory) */
 #define LBM_ENOSCRATCH -7   /* larger than the fixed scratch of lbm_wall_shear_noalloc */
+#define LBM_ETIMEOUT   -8   /* a device-side wait gave up (the step's output is invalid) */
 
 /* ---- storage of the populations ---- */
 #define LBM_FP32      0     /* f_q in FP32 */
@@ -121,11 +122,34 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes);
 int lbm_step(lbm_handle *h, int n);
 
 /* Synchronize the stream and report deferred device errors:
- * LBM_EDIVERGED, LBM_ENOTCONV (the counters are cleared when read). */
+ * LBM_EDIVERGED, LBM_ENOTCONV, LBM_ETIMEOUT (the counters are cleared when
+ * read). */
 int lbm_sync(lbm_handle *h);
 
 /* Set the CUDA stream later calls enqueue on (cudaStream_t; NULL = default). */
 int lbm_set_stream(lbm_handle *h, void *cuda_stream);
+
+/* ---- step kernel variants (all compute the same step of Algorithm 1) ---- */
+#define LBM_KERNEL_AUTO    0  /* QUAD for the 16-bit storages and PAIR for FP32 where the
+                                 grid allows, else PAIR (nx even), else CELL */
+#define LBM_KERNEL_CELL    1  /* one cell per thread, direct loads */
+#define LBM_KERNEL_PAIR    2  /* two x-adjacent cells per thread, packed FP32x2; nx even */
+#define LBM_KERNEL_STAGED  3  /* PAIR arithmetic with the pulled populations copied into
+                                 shared memory by the tensor memory accelerator (a
+                                 persistent grid, 128 x 2-cell tiles, multi-stage ring);
+                                 nx a multiple of 4 (FP32) or 8 (16-bit storage) */
+#define LBM_KERNEL_QUAD    4  /* four x-adjacent cells per thread, the x halo by warp
+                                 shuffle, PAIR arithmetic; nx a multiple of 4 */
+
+/* Choose the kernel of later steps (also the forward and recomputed steps of
+ * lbm_adjoint_step).  PAIR, QUAD and STAGED run the same arithmetic and give
+ * bit-identical states; CELL evaluates the same collision one cell at a time
+ * (the same formulas, a different FP32 operation order).  Errors: LBM_EINVAL
+ * for an unknown kind or a grid the kind does not support. */
+int lbm_set_step_kernel(lbm_handle *h, int kind);
+
+/* The kernel later steps will run (AUTO resolved) into *kind. */
+int lbm_get_step_kernel(const lbm_handle *h, int *kind);
 
 /* Statistics accumulated every stats_every steps since the last reset:
  * sums[(j*nx + i)*7 + c], c = (u, v, w, uu, vv, ww, uv), each summed over z

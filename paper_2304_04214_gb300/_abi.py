@@ -8,6 +8,10 @@ _LIB = None
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ENOTCONV, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 LBM_ENOSCRATCH = -7
+LBM_ETIMEOUT = -8
+LBM_KERNEL_AUTO, LBM_KERNEL_CELL, LBM_KERNEL_PAIR, LBM_KERNEL_STAGED, LBM_KERNEL_QUAD = 0, 1, 2, 3, 4
+KERNELS = {"auto": LBM_KERNEL_AUTO, "cell": LBM_KERNEL_CELL, "pair": LBM_KERNEL_PAIR,
+           "staged": LBM_KERNEL_STAGED, "quad": LBM_KERNEL_QUAD}
 LBM_NOALLOC_MAX_NX = 32768
 LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2
 PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16_DEV, "bf16": LBM_BF16_DEV}
@@ -52,6 +56,8 @@ PROTOTYPES = {
     "lbm_step": (ct.c_int, [_h, ct.c_int]),
     "lbm_sync": (ct.c_int, [_h]),
     "lbm_set_stream": (ct.c_int, [_h, ct.c_void_p]),
+    "lbm_set_step_kernel": (ct.c_int, [_h, ct.c_int]),
+    "lbm_get_step_kernel": (ct.c_int, [_h, ct.POINTER(ct.c_int)]),
     "lbm_stats": (ct.c_int, [_h, _dp, _dp, ct.POINTER(ct.c_long)]),
     "lbm_reset_stats": (ct.c_int, [_h]),
     "lbm_get_fields": (ct.c_int, [_h, _dp, _dp]),

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
 SOURCES = ["lbm_api.cu"]
-DEPS = ["lbm_device.cuh"]
+DEPS = ["lbm_device.cuh", "lbm_adjoint.cuh", "lbm_staged.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -29,7 +29,7 @@ class LBMChannel:
     def __init__(self, nx, ny, nz, re_tau=1000.0, n_modes=100, uniforms=None, seed=1,
                  precision="fp32", u_bulk=0.05, c_smag=0.01, kappa=0.4, B=7.8, ell_e=0.4,
                  amp=1.0, k_ratio=1.01, beta_kmin=0.5, wall_model=True, inlet=True,
-                 stats_every=0, stream=None, device=None):
+                 stats_every=0, step_kernel="auto", stream=None, device=None):
         import torch
         self._torch = torch
         self.lib = _abi.lib()
@@ -66,6 +66,8 @@ class LBMChannel:
         _abi.check(self.lib.lbm_bind_memory(self.h, ct.c_void_p(self.mem.data_ptr()),
                                             self.nbytes), "lbm_bind_memory")
         self.precision = precision
+        if step_kernel != "auto":
+            self.step_kernel = step_kernel
 
     # ---- life cycle ----
     def close(self):
@@ -97,6 +99,17 @@ class LBMChannel:
     @time.setter
     def time(self, t):
         _abi.check(self.lib.lbm_set_time(self.h, int(t)), "lbm_set_time")
+
+    @property
+    def step_kernel(self):
+        """The step kernel later steps run: 'cell', 'pair', 'quad' or 'staged'."""
+        k = ct.c_int()
+        _abi.check(self.lib.lbm_get_step_kernel(self.h, ct.byref(k)), "lbm_get_step_kernel")
+        return {v: n for n, v in _abi.KERNELS.items()}[k.value]
+
+    @step_kernel.setter
+    def step_kernel(self, name):
+        _abi.check(self.lib.lbm_set_step_kernel(self.h, _abi.KERNELS[name]), "lbm_set_step_kernel")
 
     def set_params(self, theta):
         th = np.ascontiguousarray(theta, dtype=np.float64)

@@ -4,6 +4,8 @@
 // the host, Algorithm 1 steps 1-3), carves one device arena into the two
 // lattices and the small buffers, and enqueues the kernels of
 // lbm_device.cuh on the caller's stream.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +20,7 @@
 #include "lbm.h"
 #include "lbm_adjoint.cuh"
 #include "lbm_device.cuh"
+#include "lbm_staged.cuh"
 
 namespace {
 
@@ -121,7 +124,11 @@ struct lbm_handle {
     int stg_ring = 1;
     long long stg_t0 = 0, stg_len = 0;
     long long check_every = 16;
-    bool two_cells = true;              // packed two-cell kernel when nx is even
+    int step_kind = LBM_KERNEL_AUTO;    // step kernel variant (lbm_set_step_kernel)
+    // tensor maps of the lattices the staged kernel has read (base -> map)
+    struct MapEntry { const void *base = nullptr; CUtensorMap map; };
+    MapEntry maps[32];
+    int map_next = 0;
     uint64_t *d_rate64 = nullptr;
     cudaStream_t stream = nullptr;
     long long t = 0;
@@ -131,6 +138,10 @@ struct lbm_handle {
     bool custom_profile = false;
     std::vector<double> prof_U, prof_R;
     double *d_tw = nullptr;                // [2][nx] wall-shear scratch
+    // the wall-row kernel runs beside the interior kernel on a side stream,
+    // forked from and joined back into the handle's stream every step
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float *pin_stage = nullptr;            // pinned staging of U_R and amp*chol(R): 7*ny floats
     cudaEvent_t stage_ev = nullptr;        // last upload from the staging buffer
     // instrumentation
@@ -457,8 +468,111 @@ struct StepIO {
     bool stats;
 };
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library links no driver library of its own).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// The staged kernel needs 16-byte row strides (nx a multiple of 16 / element
+// size) and the tensor-map encoder.
+bool staged_supported(const lbm_handle *h) {
+    return h->nx % (16 / (int)h->elem) == 0 && tensor_map_encoder() != nullptr;
+}
+
+int resolve_kind(const lbm_handle *h) {
+    if (h->step_kind != LBM_KERNEL_AUTO) return h->step_kind;
+    if (h->elem == 2 && h->nx % 4 == 0) return LBM_KERNEL_QUAD;
+    return h->nx % 2 == 0 ? LBM_KERNEL_PAIR : LBM_KERNEL_CELL;
+}
+
+// 4-d tensor map (x, y, z, q) of a lattice at `base`, box (BW, 2, 1, 1).
 template <class S>
-void launch_step_t(lbm_handle *h, const StepIO &io) {
+const CUtensorMap *lattice_map(lbm_handle *h, const void *base) {
+    for (auto &m : h->maps)
+        if (m.base == base) return &m.map;
+    auto &m = h->maps[h->map_next];
+    h->map_next = (h->map_next + 1) % 32;
+    const cuuint64_t e = sizeof(typename S::T);
+    const CUtensorMapDataType dt = e == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : h->opts.precision == LBM_BF16_DEV ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[4] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz, 19};
+    const cuuint64_t strides[3] = {h->nx * e, (cuuint64_t)h->nx * h->ny * e, (cuuint64_t)h->ncell * e};
+    const cuuint32_t box[4] = {(cuuint32_t)lbmk::Staged<S>::BW, (cuuint32_t)lbmk::SG_TY, 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = tensor_map_encoder()(&m.map, dt, 4, const_cast<void *>(base), dims, strides, box, es,
+                                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { m.base = nullptr; return nullptr; }
+    m.base = base;
+    return &m.map;
+}
+
+int device_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 148; }
+    if (!sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 148;
+        }
+        sms[dev] = v;
+    }
+    return sms[dev];
+}
+
+// Raise the dynamic shared-memory limit of the staged kernel<S, STATS>, once
+// per device (one set of flags per instantiation).
+template <class S, bool STATS>
+cudaError_t allow_staged_smem(int bytes) {
+    static unsigned done[2] = {0, 0};   // bit per device
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && (done[dev / 32] >> (dev % 32)) & 1u) return cudaSuccess;
+    e = cudaFuncSetAttribute(lbmk::staged_kernel<S, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && dev < 64) done[dev / 32] |= 1u << (dev % 32);
+    return e;
+}
+
+template <class S, bool STATS>
+cudaError_t launch_staged(lbm_handle *h, const lbmk::StepArgs<S> &a, const void *in) {
+    lbmk::StagedArgs<S> g;
+    const CUtensorMap *m = lattice_map<S>(h, in);
+    if (!m) return cudaErrorInvalidValue;
+    std::memcpy(&g.tmap, m, sizeof(CUtensorMap));
+    g.s = a;
+    g.nxt = (h->nx + lbmk::SG_TX - 1) / lbmk::SG_TX;
+    g.nyt = (h->ny - 2) / lbmk::SG_TY;
+    g.ntiles = g.nxt * g.nyt * h->nz;
+    constexpr int smem = lbmk::staged_smem_bytes<S, lbmk::StagedCfg<S>::STAGES>();
+    cudaError_t e = allow_staged_smem<S, STATS>(smem);
+    if (e != cudaSuccess) return e;
+    if (g.ntiles == 0) return cudaSuccess;          // ny = 4: wall rows only
+    const int nb = std::min(g.ntiles, device_sms() * lbmk::StagedCfg<S>::MINB);
+    lbmk::staged_kernel<S, STATS><<<nb, lbmk::SG_THREADS, smem, h->stream>>>(g);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
     using T = typename S::T;
     lbmk::StepArgs<S> a;
     const size_t N = (size_t)h->ncell;
@@ -485,12 +599,35 @@ void launch_step_t(lbm_handle *h, const StepIO &io) {
     const int bxmax = lbmk::STEP_THREADS / lbmk::BY;
     const size_t slot = h->prof_on ? prof_slot(h) : 0;
     if (h->prof_on) cudaEventRecord(h->ev0[slot], h->stream);
-    if (h->nx % 2 == 0 && h->two_cells) {
-        // two cells per thread
+    const int kind = resolve_kind(h);
+    cudaError_t err = cudaSuccess;
+    if (kind == LBM_KERNEL_STAGED || kind == LBM_KERNEL_PAIR || kind == LBM_KERNEL_QUAD) {
+        // the wall rows on the side stream, the interior rows on the handle's
+        // stream; both read the state of the previous step and write disjoint rows
         const int bx = (h->nx / 2) >= bxmax ? bxmax : 32;
-        dim3 block(bx, lbmk::BY), grid((h->nx / 2 + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
-        if (io.stats) lbmk::step2_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
-        else lbmk::step2_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
+        const int nbx = (h->nx / 2 + bx - 1) / bx;
+        const dim3 block(bx, lbmk::BY);
+        if ((err = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess ||
+            (err = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess)
+            return err;
+        const dim3 wgrid((h->nx + lbmk::WALL_THREADS - 1) / lbmk::WALL_THREADS, 2, h->nz);
+        if (io.stats) lbmk::wall_kernel<S, true><<<wgrid, lbmk::WALL_THREADS, 0, h->side>>>(a);
+        else lbmk::wall_kernel<S, false><<<wgrid, lbmk::WALL_THREADS, 0, h->side>>>(a);
+        if ((err = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return err;
+        if (kind == LBM_KERNEL_STAGED) {
+            err = io.stats ? launch_staged<S, true>(h, a, io.in) : launch_staged<S, false>(h, a, io.in);
+        } else if (kind == LBM_KERNEL_QUAD) {
+            const dim3 qgrid((h->nx + 127) / 128, (h->ny - 2) / lbmk::BY, h->nz), qblock(32, lbmk::BY);
+            if (io.stats) lbmk::step4_kernel<S, true><<<qgrid, qblock, 0, h->stream>>>(a);
+            else lbmk::step4_kernel<S, false><<<qgrid, qblock, 0, h->stream>>>(a);
+        } else {
+            const dim3 grid(nbx, (h->ny - 2) / lbmk::BY, h->nz);
+            if (io.stats) lbmk::step2_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
+            else lbmk::step2_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
+        }
+        cudaError_t e2 = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+        if (err == cudaSuccess) err = e2;
+        h->launches += 1;
     } else {
         const int bx = h->nx >= bxmax ? bxmax : (h->nx >= 64 && bxmax >= 64 ? 64 : 32);
         dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
@@ -499,13 +636,16 @@ void launch_step_t(lbm_handle *h, const StepIO &io) {
     }
     if (h->prof_on) cudaEventRecord(h->ev1[slot], h->stream);
     h->launches += 1;
+    return err;
 }
 
-void launch_step_io(lbm_handle *h, const StepIO &io) {
+// Enqueue one step; a launch that could not be set up (no tensor map) is
+// reported here, kernel errors by cudaGetLastError as usual.
+cudaError_t launch_step_io(lbm_handle *h, const StepIO &io) {
     switch (h->opts.precision) {
-        case LBM_FP16_DEV: launch_step_t<lbmk::StoreF16>(h, io); break;
-        case LBM_BF16_DEV: launch_step_t<lbmk::StoreBF16>(h, io); break;
-        default: launch_step_t<lbmk::StoreF32>(h, io); break;
+        case LBM_FP16_DEV: return launch_step_t<lbmk::StoreF16>(h, io);
+        case LBM_BF16_DEV: return launch_step_t<lbmk::StoreBF16>(h, io);
+        default: return launch_step_t<lbmk::StoreF32>(h, io);
     }
 }
 
@@ -539,7 +679,7 @@ int one_step(lbm_handle *h) {
     io.fw = h->d_fw;
     io.vprime = h->opts.inlet ? h->d_uin + 3 * (size_t)h->nz * h->ny * (size_t)(h->t - h->stg_t0) : h->d_uin;
     io.stats = stats;
-    launch_step_io(h, io);
+    if (cudaError_t le = launch_step_io(h, io)) return cuda_fail(le);
     if (stats) {
         h->n_samples += 1;
         const int cols = (h->nx * h->ny + lbmk::ST_COLS - 1) / lbmk::ST_COLS;
@@ -669,7 +809,6 @@ int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg, c
                        stg->uniforms ? stg->uniforms + 4 * (size_t)stg->n_modes : nullptr);
     h->theta[0] = stg->ell_e; h->theta[1] = stg->amp; h->theta[2] = opts->kappa; h->theta[3] = opts->B;
     h->opts_kappa0 = opts->kappa;
-    if (const char *v = std::getenv("LBM_GB300_ONE_CELL")) h->two_cells = v[0] == '0';
     h->elem = opts->precision == LBM_FP32 ? 4 : 2;
     h->constants();
     h->tables();
@@ -700,8 +839,13 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
         h->owns = true;
     }
     h->mem_bytes = need;
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (cudaHostAlloc((void **)&h->pin_stage, 7 * sizeof(float) * h->ny, cudaHostAllocDefault) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         if (h->owns) cudaFree(h->mem);
         h->mem = nullptr;
         return cuda_fail(cudaGetLastError());
@@ -740,17 +884,37 @@ int lbm_step(lbm_handle *h, int n) {
 int lbm_sync(lbm_handle *h) {
     if (!h) return LBM_EINVAL;
     if (!h->bound) return LBM_ESTATE;
-    unsigned fl[2] = {0, 0};
+    unsigned fl[3] = {0, 0, 0};
     cudaError_t e;
     if ((e = cudaMemcpyAsync(fl, h->d_flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
-    if (fl[0] || fl[1]) {
+    if (fl[0] || fl[1] || fl[2]) {
         if ((e = cudaMemsetAsync(h->d_flags, 0, sizeof fl, h->stream)) != cudaSuccess) return cuda_fail(e);
         cudaStreamSynchronize(h->stream);
     }
+    if (fl[2]) return LBM_ETIMEOUT;
     if (fl[1]) return LBM_EDIVERGED;
     if (fl[0]) return LBM_ENOTCONV;
+    return LBM_OK;
+}
+
+int lbm_set_step_kernel(lbm_handle *h, int kind) {
+    if (!h) return LBM_EINVAL;
+    switch (kind) {
+        case LBM_KERNEL_AUTO: case LBM_KERNEL_CELL: break;
+        case LBM_KERNEL_PAIR: if (h->nx % 2) return LBM_EINVAL; break;
+        case LBM_KERNEL_STAGED: if (!staged_supported(h)) return LBM_EINVAL; break;
+        case LBM_KERNEL_QUAD: if (h->nx % 4) return LBM_EINVAL; break;
+        default: return LBM_EINVAL;
+    }
+    h->step_kind = kind;
+    return LBM_OK;
+}
+
+int lbm_get_step_kernel(const lbm_handle *h, int *kind) {
+    if (!h || !kind) return LBM_EINVAL;
+    *kind = resolve_kind(h);
     return LBM_OK;
 }
 
@@ -1108,7 +1272,7 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
         io.utau_in = n == 0 ? A.ut_init : A.uthist + (size_t)(n - 1) * W;
         io.utau = A.uthist + (size_t)n * W;
         io.fw = h->d_fw; io.vprime = A.vwin + (size_t)n * I; io.stats = false;
-        launch_step_io(h, io);
+        if (cudaError_t le = launch_step_io(h, io)) return cuda_fail(le);
         h->t += 1;
         cur = out;
         lbmk::objective_kernel<<<obj_blocks, 128, 0, st>>>((const float *)cur, h->d_fw, A.objacc, nx, ny, nz,
@@ -1158,7 +1322,7 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
             io.utau_in = n == 0 ? A.ut_init : A.uthist + (size_t)(n - 1) * W;
             io.utau = A.ut_scr; io.fw = A.fw_scr; io.vprime = A.vwin + (size_t)n * I; io.stats = false;
             h->t = t0 + n;
-            launch_step_io(h, io);
+            if (cudaError_t le = launch_step_io(h, io)) return cuda_fail(le);
             prev = A.seg + (size_t)(m - 1) * L;
         }
         for (int n = base + K - 1; n >= base; --n) {
@@ -1210,7 +1374,7 @@ int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, 
     StepIO io;
     io.in = h->lat[h->cur]; io.out = A.lamB; io.utau = A.ut_scr; io.fw = A.fw_scr; io.vprime = A.vwin;
     io.stats = false;
-    launch_step_io(h, io);
+    if (cudaError_t le = launch_step_io(h, io)) return cuda_fail(le);
     std::vector<float> buf(L);
     for (size_t c = 0; c < L; ++c) buf[c] = (float)lambda_next[c];
     if ((e = cudaMemcpyAsync(A.lamA, buf.data(), L * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -1238,6 +1402,9 @@ void lbm_destroy(lbm_handle *h) {
     if (h->owns && h->mem) cudaFree(h->mem);
     if (h->pin_stage) cudaFreeHost(h->pin_stage);
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
 }
 
@@ -1251,6 +1418,7 @@ const char *lbm_error_string(int code) {
         case LBM_ENOTCONV: return "u_tau Newton solve did not converge";
         case LBM_ESTATE: return "call out of order";
         case LBM_ENOSCRATCH: return "size exceeds the fixed scratch of a no-allocation call";
+        case LBM_ETIMEOUT: return "a device-side wait timed out";
         default: return "unknown error";
     }
 }

@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace lbmk {
 
@@ -45,7 +46,8 @@ constexpr float S_M = 1.98f;     // moments 16, 17, 18
 // hold the deviation f - w_q.  SHIFTED tells the collision which of the two
 // its registers hold (the arithmetic is FP32 either way).
 // ---------------------------------------------------------------------------
-// ld2 / st2 move two adjacent populations (even offset) in one access.
+// ld2 / st2 move two adjacent populations (even offset) in one access, ld4 /
+// st4 four (offset a multiple of four).
 struct StoreF32 {
     using T = float;
     static constexpr bool SHIFTED = false;
@@ -53,6 +55,8 @@ struct StoreF32 {
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
     static __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
     static __device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+    static __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+    static __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 };
 struct StoreF16 {
     using T = __half;
@@ -65,6 +69,19 @@ struct StoreF16 {
     static __device__ __forceinline__ void st2(__half *p, float2 v) {
         *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v);
     }
+    static __device__ __forceinline__ float4 ld4(const __half *p) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        __half2 lo, hi;
+        memcpy(&lo, &u.x, 4); memcpy(&hi, &u.y, 4);
+        const float2 a = __half22float2(lo), b = __half22float2(hi);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ void st4(__half *p, float4 v) {
+        const __half2 lo = __float22half2_rn(make_float2(v.x, v.y)), hi = __float22half2_rn(make_float2(v.z, v.w));
+        uint2 u;
+        memcpy(&u.x, &lo, 4); memcpy(&u.y, &hi, 4);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
@@ -76,6 +93,20 @@ struct StoreBF16 {
     }
     static __device__ __forceinline__ void st2(__nv_bfloat16 *p, float2 v) {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
+    }
+    static __device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        __nv_bfloat162 lo, hi;
+        memcpy(&lo, &u.x, 4); memcpy(&hi, &u.y, 4);
+        const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ void st4(__nv_bfloat16 *p, float4 v) {
+        const __nv_bfloat162 lo = __float22bfloat162_rn(make_float2(v.x, v.y));
+        const __nv_bfloat162 hi = __float22bfloat162_rn(make_float2(v.z, v.w));
+        uint2 u;
+        memcpy(&u.x, &lo, 4); memcpy(&u.y, &hi, 4);
+        *reinterpret_cast<uint2 *>(p) = u;
     }
 };
 
@@ -115,6 +146,11 @@ __device__ __forceinline__ double reichardt_dy_d(double yp, double kap, double B
 
 // Newton solve of eq:u_tau_implicit, u u+(y1 u / nu) = uhat, uhat > 0, warm
 // started; FP32 first, FP64 if FP32 did not settle.  *ok = false if neither did.
+// FP32 stops after a step |du| <= 2e-4 u: the error after a Newton step is
+// about (u R''/2R') (du/u)^2 u, and u R''/2R' of this law lies between 0.06
+// (log layer) and 0.5 (viscous sublayer), so the returned value is within
+// 2e-8 u of the root -- below FP32 rounding.  From the previous step's u_tau
+// that is usually one step.
 __device__ __forceinline__ float solve_utau_dev(float uhat, float y1_nu, float kap, float B, float guess,
                                              bool *ok) {
     float u = guess > 0.0f ? guess : 1e-3f;
@@ -123,10 +159,10 @@ __device__ __forceinline__ float solve_utau_dev(float uhat, float y1_nu, float k
         const float up = reichardt_f(yp, kap, B);
         const float r = u * up - uhat;
         const float dr = up + yp * reichardt_dy_f(yp, kap, B);
-        const float du = r / dr;
+        const float du = r * rcp_approx(dr);
         float un = u - du;
         if (!(un > 0.0f)) un = 0.5f * u;
-        if (fabsf(du) <= 4e-7f * un) { *ok = true; return un; }
+        if (fabsf(du) <= 2e-4f * un) { *ok = true; return un; }
         u = un;
     }
     double ud = u;
@@ -305,29 +341,47 @@ __device__ __forceinline__ V2 vfma(float a, V2 b, V2 c) { return __ffma2_rn(vdup
 __device__ __forceinline__ V2 vrcp(V2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
 __device__ __forceinline__ V2 vsqrt(V2 a) { return make_float2(sqrt_approx(a.x), sqrt_approx(a.y)); }
 
-// Force-free MRT-LES collision of two cells (interior rows): the same
-// algebra as collide_mrt<SHIFTED, false>, written with fused packed operations.
+// Pair sums / differences, density and momentum of two cells (eq:density,
+// eq:momentum without the force).
+struct Pairs2 {
+    V2 s[9], d[9], f9;
+    V2 s04, s13, s57, s26, Sdg, Sax;
+    V2 rho, jx, jy, jz;
+};
 template <bool SHIFTED>
-__device__ __forceinline__ void collide_mrt2(V2 (&f)[19], float tau0, float csm18, V2 &ux_o, V2 &uy_o,
-                                             V2 &uz_o) {
-    V2 s[9], d[9];
+__device__ __forceinline__ void make_pairs2(const V2 (&f)[19], Pairs2 &P) {
 #pragma unroll
-    for (int p = 0; p < 9; ++p) { s[p] = f[p] + f[18 - p]; d[p] = f[p] - f[18 - p]; }
-    const V2 f9 = f[9];
-    const V2 s04 = s[0] + s[4], s13 = s[1] + s[3], s57 = s[5] + s[7], s26 = s[2] + s[6];
-    const V2 Sdg = (s04 + s13) + s57;
-    const V2 Sax = s26 + s[8];
-    // rho and momentum (eq:density, eq:momentum)
-    const V2 rho = SHIFTED ? (Sdg + Sax) + f9 + vdup(1.0f) : (Sdg + Sax) + f9;
+    for (int p = 0; p < 9; ++p) { P.s[p] = f[p] + f[18 - p]; P.d[p] = f[p] - f[18 - p]; }
+    const V2 *s = P.s, *d = P.d;
+    P.f9 = f[9];
+    P.s04 = s[0] + s[4]; P.s13 = s[1] + s[3]; P.s57 = s[5] + s[7]; P.s26 = s[2] + s[6];
+    P.Sdg = (P.s04 + P.s13) + P.s57;
+    P.Sax = P.s26 + s[8];
+    P.rho = SHIFTED ? (P.Sdg + P.Sax) + P.f9 + vdup(1.0f) : (P.Sdg + P.Sax) + P.f9;
     const V2 Dx = (d[3] - d[1]) + (d[7] - d[5]);
     const V2 Dy = (d[4] - d[0]) - (d[5] + d[7]);
     const V2 Dz = -(d[0] + d[4]) - (d[1] + d[3]);
-    const V2 jx = Dx - d[8], jy = Dy - d[6], jz = Dz - d[2];
+    P.jx = Dx - d[8]; P.jy = Dy - d[6]; P.jz = Dz - d[2];
+}
+
+// MRT-LES collision of two cells: the algebra of collide_mrt written with
+// fused packed operations.  HAS_FORCE adds the moment-space Guo source of a
+// wall force (Fx, 0, Fz) per cell -- the wall-model force is tangential, so
+// its y component is zero by construction (eq:force_wm, the wall normal is y).
+template <bool SHIFTED, bool HAS_FORCE>
+__device__ __forceinline__ void collide_pairs2(const Pairs2 &P, V2 (&f)[19], V2 Fx, V2 Fz, float tau0,
+                                               float csm18, V2 &ux_o, V2 &uy_o, V2 &uz_o) {
+    const V2 *s = P.s, *d = P.d;
+    const V2 f9 = P.f9, s04 = P.s04, s13 = P.s13, s57 = P.s57, s26 = P.s26;
+    const V2 Sdg = P.Sdg, Sax = P.Sax, rho = P.rho, jx = P.jx, jy = P.jy, jz = P.jz;
     const V2 irho = vrcp(rho);
-    const V2 ux = jx * irho, uy = jy * irho, uz = jz * irho;
+    // eq:momentum: rho u = sum f c + F/2
+    const V2 rux = HAS_FORCE ? vfma(0.5f, Fx, jx) : jx;
+    const V2 ruz = HAS_FORCE ? vfma(0.5f, Fz, jz) : jz;
+    const V2 ux = rux * irho, uy = jy * irho, uz = ruz * irho;
     ux_o = ux; uy_o = uy; uz_o = uz;
-    const V2 uxx = jx * ux, uyy = jy * uy, uzz = jz * uz;
-    const V2 uxy = jx * uy, uyz = jy * uz, uxz = jx * uz;
+    const V2 uxx = rux * ux, uyy = jy * uy, uzz = ruz * uz;
+    const V2 uxy = rux * uy, uyz = jy * uz, uxz = rux * uz;
     const V2 usq = (uxx + uyy) + uzz;
     // non-equilibrium moments; M w = (1, -11, 3, 0, ...) sets the constants
     const V2 e1 = vfma(-30.0f, f9, vfma(8.0f, Sdg, -11.0f * Sax));
@@ -336,9 +390,9 @@ __device__ __forceinline__ void collide_mrt2(V2 (&f)[19], float tau0, float csm1
     const V2 r3 = SHIFTED ? -3.0f * (rho - vdup(1.0f)) : -3.0f * rho;
     const V2 n1 = vfma(-19.0f, usq, e1 + r11);
     const V2 n2 = vfma(5.5f, usq, e2 + r3);
-    const V2 n4 = vfma(5.0f, d[8], vfma(2.0f / 3.0f, jx, jx));
+    const V2 n4 = vfma(5.0f, d[8], vfma(2.0f / 3.0f, rux, jx));
     const V2 n6 = vfma(5.0f, d[6], vfma(2.0f / 3.0f, jy, jy));
-    const V2 n8 = vfma(5.0f, d[2], vfma(2.0f / 3.0f, jz, jz));
+    const V2 n8 = vfma(5.0f, d[2], vfma(2.0f / 3.0f, ruz, jz));
     const V2 pxx_eq = vfma(2.0f, uxx, -(uyy + uzz));
     const V2 pww_eq = uyy - uzz;
     const V2 t1357 = s13 + s57;
@@ -364,15 +418,39 @@ __device__ __forceinline__ void collide_mrt2(V2 (&f)[19], float tau0, float csm1
     const V2 tt = vdup(tau0);
     const V2 sv = 2.0f * vrcp(tt + vsqrt(vfma(csm18 * vsqrt(qq), irho, tt * tt)));
     // relaxation: G_k = s_k n_k / |row_k|^2
-    const V2 G1 = n1 * (S_E / 2394.0f), G2 = n2 * (S_EPS / 252.0f);
-    const V2 G4 = n4 * (S_Q / 40.0f), G6 = n6 * (S_Q / 40.0f), G8 = n8 * (S_Q / 40.0f);
+    V2 G1 = n1 * (S_E / 2394.0f), G2 = n2 * (S_EPS / 252.0f);
+    V2 G4 = n4 * (S_Q / 40.0f), G6 = n6 * (S_Q / 40.0f), G8 = n8 * (S_Q / 40.0f);
     const V2 sv36 = sv * (1.0f / 36.0f), sv12 = sv * (1.0f / 12.0f), sv4 = sv * 0.25f;
-    const V2 G9 = sv36 * n9, G10 = n10 * (S_PI / 72.0f);
-    const V2 G11 = sv12 * n11, G12 = n12 * (S_PI / 24.0f);
-    const V2 G13 = sv4 * n13, G14 = sv4 * n14, G15 = sv4 * n15;
+    V2 G9 = sv36 * n9, G10 = n10 * (S_PI / 72.0f);
+    V2 G11 = sv12 * n11, G12 = n12 * (S_PI / 24.0f);
+    V2 G13 = sv4 * n13, G14 = sv4 * n14, G15 = sv4 * n15;
     const V2 G16 = n16 * (S_M * 0.125f), G17 = n17 * (S_M * 0.125f), G18 = n18 * (S_M * 0.125f);
-    // f* = f - M^T g by opposite pairs (no force: G3 = G5 = G7 = 0), rebuilt
-    // from the pair sums: f*_p = (s_p/2 - E) + (d_p/2 - O), f*_{18-p} = (s_p/2 - E) - (d_p/2 - O)
+    // odd parts of the conserved-momentum rows (G3, G5, G7) and the heat fluxes
+    V2 Jx = G4, Jz = G8, Ox = 4.0f * G4, Oz = 4.0f * G8;
+    const V2 Jy = G6, Oy = 4.0f * G6;
+    if (HAS_FORCE) {
+        // moments of the Guo source M F~ (second-order Hermite form), F_y = 0
+        const V2 uF = vfma(ux, Fx, uz * Fz);
+        const V2 hv = vfma(-0.5f, sv, vdup(1.0f));
+        const float cq = (1.0f - 0.5f * S_Q) * (2.0f / 3.0f) * (1.0f / 40.0f);
+        const V2 F9 = vfma(4.0f, ux * Fx, -2.0f * (uz * Fz));
+        const V2 F11 = -2.0f * (uz * Fz);
+        G1 = vfma(-(1.0f - 0.5f * S_E) * 38.0f / 2394.0f, uF, G1);
+        G2 = vfma((1.0f - 0.5f * S_EPS) * 11.0f / 252.0f, uF, G2);
+        G4 = vfma(cq, Fx, G4); G8 = vfma(cq, Fz, G8);
+        G9 = G9 - hv * F9 * (1.0f / 36.0f);
+        G10 = vfma((1.0f - 0.5f * S_PI) * 0.5f / 72.0f, F9, G10);
+        G11 = G11 - hv * F11 * (1.0f / 12.0f);
+        G12 = vfma((1.0f - 0.5f * S_PI) * 0.5f / 24.0f, F11, G12);
+        G13 = G13 - hv * (uy * Fx) * 0.25f;
+        G14 = G14 - hv * (uy * Fz) * 0.25f;
+        G15 = G15 - hv * vfma(ux, Fz, uz * Fx) * 0.25f;
+        const V2 G3 = -0.1f * Fx, G7 = -0.1f * Fz;
+        Jx = G3 + G4; Jz = G7 + G8;
+        Ox = vfma(4.0f, G4, -G3); Oz = vfma(4.0f, G8, -G7);
+    }
+    // f* = f - M^T g by opposite pairs, rebuilt from the pair sums:
+    // f*_p = (s_p/2 - E) + (d_p/2 - O), f*_{18-p} = (s_p/2 - E) - (d_p/2 - O)
     const V2 Aax = vfma(-11.0f, G1, -4.0f * G2);
     const V2 Ddg = vfma(8.0f, G1, G2);
     const V2 g9_10 = G9 + G10, g11_12 = G11 + G12;
@@ -384,16 +462,25 @@ __device__ __forceinline__ void collide_mrt2(V2 (&f)[19], float tau0, float csm1
         f[p] = hs + hd;
         f[18 - p] = hs - hd;
     };
-    put(0, Xa + G14, (G18 - G17) - (G6 + G8));
-    put(1, Xb + G15, (G16 - G18) - (G4 + G8));
-    put(2, vfma(2.0f, G10 + G12, Aax - (G9 + G11)), 4.0f * G8);
-    put(3, Xb - G15, (G4 - G8) - (G16 + G18));
-    put(4, Xa - G14, (G6 - G8) + (G17 + G18));
-    put(5, Xc + G13, (G17 - G16) - (G4 + G6));
-    put(6, vfma(2.0f, G10 - G12, (Aax - G9) + G11), 4.0f * G6);
-    put(7, Xc - G13, (G4 - G6) + (G16 + G17));
-    put(8, vfma(2.0f, G9, vfma(-4.0f, G10, Aax)), 4.0f * G4);
+    put(0, Xa + G14, (G18 - G17) - (Jy + Jz));
+    put(1, Xb + G15, (G16 - G18) - (Jx + Jz));
+    put(2, vfma(2.0f, G10 + G12, Aax - (G9 + G11)), Oz);
+    put(3, Xb - G15, (Jx - Jz) - (G16 + G18));
+    put(4, Xa - G14, (Jy - Jz) + (G17 + G18));
+    put(5, Xc + G13, (G17 - G16) - (Jx + Jy));
+    put(6, vfma(2.0f, G10 - G12, (Aax - G9) + G11), Oy);
+    put(7, Xc - G13, (Jx - Jy) + (G16 + G17));
+    put(8, vfma(2.0f, G9, vfma(-4.0f, G10, Aax)), Ox);
     f[9] = vfma(30.0f, G1, vfma(-12.0f, G2, f9));
+}
+
+// Force-free collision of two cells (interior rows).
+template <bool SHIFTED>
+__device__ __forceinline__ void collide_mrt2(V2 (&f)[19], float tau0, float csm18, V2 &ux_o, V2 &uy_o,
+                                             V2 &uz_o) {
+    Pairs2 P;
+    make_pairs2<SHIFTED>(f, P);
+    collide_pairs2<SHIFTED, false>(P, f, vdup(0.0f), vdup(0.0f), tau0, csm18, ux_o, uy_o, uz_o);
 }
 
 // ---------------------------------------------------------------------------
@@ -443,6 +530,7 @@ struct StepArgs {
 };
 
 constexpr int BY = 2;  // rows per block: (0,1) and (ny-2,ny-1) share a block
+constexpr int WALL_THREADS = 128;   // threads (x-cells) per block of the wall-row kernel
 #ifndef LBM_STEP_THREADS
 #define LBM_STEP_THREADS 128   // threads per block of the step kernel (BX x BY)
 #endif
@@ -550,10 +638,11 @@ __device__ __forceinline__ void finish_cell(const StepArgs<S> &a, const float (&
 // The first and last block rows: the cells next to the slip walls (mirrored
 // pulls) and the wall model (Sec. 2.3, Algorithm 1 steps 9-14) on the first
 // off-wall cells, whose second cell sits in the same block.  Kept out of line
-// so that the interior path gets its own register allocation.
+// so that the interior path gets its own register allocation.  The nthr
+// threads that call it (a multiple of 32) meet at named barrier 1.
 template <class S, bool STATS>
 __device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k, int tx, int o00, int ozm,
-                                       int ozp, int ic, int xm, int xp) {
+                                       int ozp, int ic, int xm, int xp, int nthr) {
     __shared__ float su2[2 * STEP_THREADS / BY][3];   // slot tx (one or two per thread)
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const bool bot = j == 0, top = j == ny - 1;
@@ -571,7 +660,7 @@ __device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k
     if (a.wall_model) {                                   // block-uniform
         const float irho = 1.0f / (1.0f + P.drho);
         if (!is_wall) { su2[tx][0] = P.jx * irho; su2[tx][1] = P.jy * irho; su2[tx][2] = P.jz * irho; }
-        __syncthreads();
+        asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
         if (is_wall && valid) {
             const int w = bot ? 0 : 1;
             const float u2x = su2[tx][0], u2z = su2[tx][2];
@@ -631,7 +720,7 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, LBM_STEP_MINB) step_kernel(c
     const int o00 = (k * ny + j) * nx;
 
     if (byi == 0 || byi == gridDim.y - 1) {               // block-uniform
-        wall_rows<S, STATS>(a, i, j, k, tx, o00, ozm, ozp, ic, xm, xp);
+        wall_rows<S, STATS>(a, i, j, k, tx, o00, ozm, ozp, ic, xm, xp, blockDim.x * blockDim.y);
         return;
     }
     float f[19];
@@ -644,10 +733,121 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, LBM_STEP_MINB) step_kernel(c
     if (i < nx) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
 }
 
-// Two x-adjacent cells (i, i+1), i even, per thread: vector loads for the
-// populations with c_x = 0, two scalar loads for the shifted ones, packed FP32x2
-// arithmetic, vector stores.  nx must be even.  The first and last block rows
-// run the scalar wall path once per cell.
+// Load the pulled populations of two x-adjacent cells (i0, i0 + 1) of the
+// interior row whose offset is o00 (row start in its plane): vector loads where
+// c_x = 0, two scalar loads where c_x != 0.  ozm / ozp: plane shifts of the
+// c_z = +1 / -1 sources (periodic z); the rows of the c_y = +1 / -1 sources are
+// o00 -/+ nx.  xm0 / xp1: the sources of the lo cell's c_x = +1 and the hi
+// cell's c_x = -1 populations.
+template <class S>
+__device__ __forceinline__ void load_pair(const StepArgs<S> &a, V2 (&f)[19], int o00, int ozm, int ozp, int ic,
+                                          int xm0, int xp1) {
+    const int rm = o00 - a.nx, rp = o00 + a.nx;      // rows for c_y = +1 / -1
+#define LD_C0(q, row) f[q] = S::ld2(a.in[q] + (row) + ic)
+#define LD_CP(q, row) f[q] = make_float2(S::ld(a.in[q] + (row) + xm0), S::ld(a.in[q] + (row) + ic))
+#define LD_CM(q, row) f[q] = make_float2(S::ld(a.in[q] + (row) + ic + 1), S::ld(a.in[q] + (row) + xp1))
+    LD_C0(0, rp + ozp); LD_CM(1, o00 + ozp); LD_C0(2, o00 + ozp); LD_CP(3, o00 + ozp); LD_C0(4, rm + ozp);
+    LD_CM(5, rp);       LD_C0(6, rp);        LD_CP(7, rp);        LD_CM(8, o00);       LD_C0(9, o00);
+    LD_CP(10, o00);     LD_CM(11, rm);       LD_C0(12, rm);       LD_CP(13, rm);       LD_C0(14, rp + ozm);
+    LD_CM(15, o00 + ozm); LD_C0(16, o00 + ozm); LD_CP(17, o00 + ozm); LD_C0(18, rm + ozm);
+#undef LD_C0
+#undef LD_CP
+#undef LD_CM
+}
+
+// Inlet velocity u_in = (U_R, 0, 0) + a v' of row j, plane k (eq:u_couple, eq:v_fluc).
+template <class S>
+__device__ __forceinline__ void inlet_velocity(const StepArgs<S> &a, int j, int k, float &vx, float &vy,
+                                               float &vz) {
+    const float *vp = a.vprime + ((size_t)k * a.ny + j) * 3;
+    const float *m = a.amat + 6 * j;
+    vx = a.UR[j] + m[0] * vp[0];
+    vy = m[1] * vp[0] + m[2] * vp[1];
+    vz = m[3] * vp[0] + m[4] * vp[1] + m[5] * vp[2];
+}
+
+// The wall rows j = 0 and j = ny - 1 of the step, one cell per thread: block
+// = 128 x-cells of one wall row (blockIdx.y = 0 bottom, 1 top) and plane
+// blockIdx.z.  Launched beside the interior kernel (the rows are disjoint).
+// The Newton solve makes these threads latency-bound, so each does one cell:
+// both sets of pulled populations (its own, mirrored at the wall, and the
+// second cell's for u_2) are loaded up front, then the wall model and the
+// scalar collision with the wall force.
+template <class S, bool STATS>
+__global__ void __launch_bounds__(WALL_THREADS) wall_kernel(const __grid_constant__ StepArgs<S> a) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool bot = blockIdx.y == 0;
+    const int j = bot ? 0 : ny - 1, j2 = bot ? 1 : ny - 2, w = bot ? 0 : 1;
+    const int k = blockIdx.z;
+    const bool valid = i < nx;
+    const int ic = valid ? i : nx - 1;
+    int xm = ic - 1, xp = ic + 1;                    // sources for c_x = +1 / -1
+    if (a.inlet) { xm = max(xm, 0); xp = min(xp, nx - 1); }
+    else { xm = xm < 0 ? nx - 1 : xm; xp = xp >= nx ? 0 : xp; }
+    const int plane = nx * ny;
+    const int ozm = k == 0 ? (nz - 1) * plane : -plane;       // source plane for c_z = +1
+    const int ozp = k == nz - 1 ? -(nz - 1) * plane : plane;  // source plane for c_z = -1
+    const int o00 = (k * ny + j) * nx, o2 = (k * ny + j2) * nx;
+    float f[19], g[19];
+    load_pulled<S, true>(a, f, o00, ozm, ozp, bot ? 0 : -nx, bot ? nx : 0, ic, xm, xp, bot, !bot);
+    if (a.wall_model) load_pulled<S, false>(a, g, o2, ozm, ozp, -nx, nx, ic, xm, xp, false, false);
+    const bool inlet_cell = a.inlet && i == 0;
+    if (inlet_cell) inlet_rebuild<S>(a, f, j, k);
+    Pairs P;
+    make_pairs<S::SHIFTED>(f, P);
+    float Fx = 0.0f, Fz = 0.0f;
+    if (a.wall_model) {
+        // u_2 of the second cell: tangential momentum over density (at the
+        // inlet: u_in, the velocity its regularized rebuild gives)
+        float u2x, u2z;
+        if (inlet_cell) {
+            float vy;
+            inlet_velocity<S>(a, j2, k, u2x, vy, u2z);
+        } else {
+            Pairs P2;
+            make_pairs<S::SHIFTED>(g, P2);
+            const float ir2 = rcp_approx(1.0f + P2.drho);
+            u2x = P2.jx * ir2; u2z = P2.jz * ir2;
+        }
+        // eq:base: e_x from the tangential part of u_2 (the wall normal is y);
+        // eq:uhat with the first-cell velocity; Newton for u_tau; tau_w = rho u_tau^2
+        const float tn = sqrtf(u2x * u2x + u2z * u2z);
+        const size_t iu = ((size_t)w * nz + k) * nx + ic;
+        float ut_new = a.utau_in[iu];
+        if (tn >= 1e-12f) {
+            const float itn = rcp_approx(tn);
+            const float ex = u2x * itn, ez = u2z * itn;
+            const float rho = 1.0f + P.drho;
+            const float uhat = (P.jx * ex + P.jz * ez) * rcp_approx(rho);
+            const float sg = uhat < 0.0f ? -1.0f : 1.0f;
+            const float ua = fabsf(uhat);
+            float ut = 0.0f;
+            if (ua > 0.0f && valid) {
+                bool ok;
+                ut = solve_utau_dev(ua, a.y1_nu, a.kappa, a.B, ut_new, &ok);
+                if (!ok) atomicAdd(a.flags, 1u);
+            }
+            ut_new = ut;
+            const float tw = rho * ut * ut * sg;          // eq:force_wm with A = 1
+            Fx = -tw * ex; Fz = -tw * ez;
+        }
+        if (valid) {
+            a.utau[iu] = ut_new;
+            float *fwp = a.fw + (((size_t)w * nz + k) * nx + i) * 3;
+            fwp[0] = Fx; fwp[1] = 0.0f; fwp[2] = Fz;
+        }
+    }
+    float ux, uy, uz;
+    if (a.wall_model) collide_mrt<S::SHIFTED, true>(f, P, Fx, 0.0f, Fz, a.tau0, a.csm18, ux, uy, uz);
+    else collide_mrt<S::SHIFTED, false>(f, P, 0.0f, 0.0f, 0.0f, a.tau0, a.csm18, ux, uy, uz);
+    if (valid) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
+}
+
+// Interior rows 1 .. ny - 2, two x-adjacent cells (i, i+1), i even, per
+// thread: vector loads for the populations with c_x = 0, two scalar loads for
+// the shifted ones, packed FP32x2 arithmetic, vector stores.  nx must be even.
+// Grid (x range, row pair, plane).
 // Resident blocks per SM the register budget aims for: FP32 storage is bound
 // by memory latency at five, the 16-bit formats move half the bytes and gain
 // from the sixth block's extra warps.
@@ -662,47 +862,25 @@ template <> struct Step2Blocks<StoreF32> { static constexpr int value = LBM_STEP
 
 template <class S, bool STATS>
 __global__ void __launch_bounds__(LBM_STEP_THREADS, Step2Blocks<S>::value) step2_kernel(const __grid_constant__ StepArgs<S> a) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nx = a.nx, ny = a.ny;
     const int tx = threadIdx.x, ty = threadIdx.y;
+    // every other step walks the blocks backwards, so that a step starts on
+    // the planes the previous step wrote last (still in L2)
     const int bxi = a.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
     const int byi = a.reverse ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
-    const int i0 = 2 * (bxi * blockDim.x + tx);
-    const int j = byi * BY + ty;
     const int k = a.reverse ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
-    const int plane = nx * ny;
-    const int ozm = k == 0 ? (nz - 1) * plane : -plane;      // source plane for c_z = +1
-    const int ozp = k == nz - 1 ? -(nz - 1) * plane : plane;  // source plane for c_z = -1
-    const int o00 = (k * ny + j) * nx;
-
-    if (byi == 0 || byi == gridDim.y - 1) {               // block-uniform: scalar wall path per cell
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            const int i = i0 + h;
-            const int ic = i < nx ? i : nx - 1;
-            int xm = ic - 1, xp = ic + 1;
-            if (a.inlet) { xm = max(xm, 0); xp = min(xp, nx - 1); }
-            else { xm = xm < 0 ? nx - 1 : xm; xp = xp >= nx ? 0 : xp; }
-            wall_rows<S, STATS>(a, i, j, k, tx + h * blockDim.x, o00, ozm, ozp, ic, xm, xp);
-        }
-        return;
-    }
+    const int i0 = 2 * (bxi * blockDim.x + tx);
+    const int j = 1 + byi * BY + ty;
     const bool valid = i0 < nx;
     const int ic = valid ? i0 : nx - 2;
     int xm0 = ic - 1, xp1 = ic + 2;                  // lo cell's c_x=+1 source, hi cell's c_x=-1 source
     if (a.inlet) { xm0 = max(xm0, 0); xp1 = min(xp1, nx - 1); }
     else { xm0 = xm0 < 0 ? nx - 1 : xm0; xp1 = xp1 >= nx ? 0 : xp1; }
-    const int rm = o00 - nx, rp = o00 + nx;          // rows for c_y = +1 / -1
+    const int plane = nx * ny;
+    const int ozm = k == 0 ? (a.nz - 1) * plane : -plane;      // source plane for c_z = +1
+    const int ozp = k == a.nz - 1 ? -(a.nz - 1) * plane : plane;  // source plane for c_z = -1
     V2 f[19];
-#define LD_C0(q, row) f[q] = S::ld2(a.in[q] + (row) + ic)
-#define LD_CP(q, row) f[q] = make_float2(S::ld(a.in[q] + (row) + xm0), S::ld(a.in[q] + (row) + ic))
-#define LD_CM(q, row) f[q] = make_float2(S::ld(a.in[q] + (row) + ic + 1), S::ld(a.in[q] + (row) + xp1))
-    LD_C0(0, rp + ozp); LD_CM(1, o00 + ozp); LD_C0(2, o00 + ozp); LD_CP(3, o00 + ozp); LD_C0(4, rm + ozp);
-    LD_CM(5, rp);       LD_C0(6, rp);        LD_CP(7, rp);        LD_CM(8, o00);       LD_C0(9, o00);
-    LD_CP(10, o00);     LD_CM(11, rm);       LD_C0(12, rm);       LD_CP(13, rm);       LD_C0(14, rp + ozm);
-    LD_CM(15, o00 + ozm); LD_C0(16, o00 + ozm); LD_CP(17, o00 + ozm); LD_C0(18, rm + ozm);
-#undef LD_C0
-#undef LD_CP
-#undef LD_CM
+    load_pair<S>(a, f, (k * ny + j) * nx, ozm, ozp, ic, xm0, xp1);
     if (a.inlet && i0 == 0) {                        // the lo cell is an inlet cell
         float fl[19];
 #pragma unroll
@@ -714,11 +892,11 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, Step2Blocks<S>::value) step2
     V2 ux, uy, uz;
     collide_mrt2<S::SHIFTED>(f, a.tau0, a.csm18, ux, uy, uz);
     if (!valid) return;
-    const int c = o00 + ic;
+    const int c = (k * ny + j) * nx + ic;
 #pragma unroll
     for (int q = 0; q < 19; ++q) S::st2(a.out[q] + c, f[q]);
     if (STATS) {
-        const long long N = (long long)plane * nz;
+        const long long N = (long long)nx * ny * a.nz;
         *reinterpret_cast<float2 *>(a.ubuf + c) = ux;
         *reinterpret_cast<float2 *>(a.ubuf + N + c) = uy;
         *reinterpret_cast<float2 *>(a.ubuf + 2 * N + c) = uz;
@@ -726,6 +904,86 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, Step2Blocks<S>::value) step2
     if (a.check) {
         const V2 uu = vfma(ux, ux, vfma(uy, uy, uz * uz));
         if (!(uu.x < 0.09f) || !(uu.y < 0.09f)) atomicAdd(a.flags + 1, 1u);   // also catches NaN
+    }
+}
+
+// Interior rows, four x-adjacent cells (x0 .. x0 + 3, x0 a multiple of four)
+// per thread: one vector load per direction, the x halo (x0 - 1 for c_x = +1,
+// x0 + 4 for c_x = -1) from the neighbouring lane by a warp shuffle -- lanes 0
+// and 31 and the lattice ends load theirs -- two packed collisions, one vector
+// store per direction.  Per cell this halves the address arithmetic, loads
+// and stores of step2_kernel, which is what bounds the 16-bit storages.
+// nx must be a multiple of four.  Block (32, 2): a warp is 128 cells of a row.
+#ifndef LBM_STEP4_MINB
+#define LBM_STEP4_MINB 4
+#endif
+template <class S, bool STATS>
+__global__ void __launch_bounds__(64, 2 * LBM_STEP4_MINB) step4_kernel(const __grid_constant__ StepArgs<S> a) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int bxi = a.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int byi = a.reverse ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+    const int k = a.reverse ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    const int x0 = 4 * (bxi * 32 + lane);
+    const int j = 1 + byi * BY + ty;
+    const bool valid = x0 < nx;
+    const int xc = valid ? x0 : nx - 4;
+    // halo sources: x0 - 1 and x0 + 4 with the x boundary rule
+    int xm = xc - 1, xp = xc + 4;
+    if (a.inlet) { xm = max(xm, 0); xp = min(xp, nx - 1); }
+    else { xm = xm < 0 ? nx - 1 : xm; xp = xp >= nx ? 0 : xp; }
+    const bool own_left = lane == 0 || x0 == 0;       // cannot take x0 - 1 from lane - 1
+    const bool own_right = lane == 31 || x0 + 4 >= nx;  // nor x0 + 4 from lane + 1
+    const int plane = nx * ny;
+    const int ozm = k == 0 ? (nz - 1) * plane : -plane;       // source plane for c_z = +1
+    const int ozp = k == nz - 1 ? -(nz - 1) * plane : plane;  // source plane for c_z = -1
+    const int o00 = (k * ny + j) * nx, rm = o00 - nx, rp = o00 + nx;
+    V2 fa[19], fb[19];                                // cells (x0, x0+1), (x0+2, x0+3)
+    auto quad = [&](int q, int row) {
+        const typename S::T *r = a.in[q] + row;
+        const float4 v = S::ld4(r + xc);
+        if (CX(q) == 0) {
+            fa[q] = make_float2(v.x, v.y); fb[q] = make_float2(v.z, v.w);
+        } else if (CX(q) > 0) {                       // source x - 1
+            float left = __shfl_up_sync(0xffffffffu, v.w, 1);
+            if (own_left) left = S::ld(r + xm);
+            fa[q] = make_float2(left, v.x); fb[q] = make_float2(v.y, v.z);
+        } else {                                      // source x + 1
+            float right = __shfl_down_sync(0xffffffffu, v.x, 1);
+            if (own_right) right = S::ld(r + xp);
+            fa[q] = make_float2(v.y, v.z); fb[q] = make_float2(v.w, right);
+        }
+    };
+    quad(0, rp + ozp); quad(1, o00 + ozp); quad(2, o00 + ozp); quad(3, o00 + ozp); quad(4, rm + ozp);
+    quad(5, rp);       quad(6, rp);        quad(7, rp);        quad(8, o00);       quad(9, o00);
+    quad(10, o00);     quad(11, rm);       quad(12, rm);       quad(13, rm);       quad(14, rp + ozm);
+    quad(15, o00 + ozm); quad(16, o00 + ozm); quad(17, o00 + ozm); quad(18, rm + ozm);
+    if (a.inlet && x0 == 0) {                        // cell x0 is an inlet cell
+        float fl[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) fl[q] = fa[q].x;
+        inlet_rebuild<S>(a, fl, j, k);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) fa[q].x = fl[q];
+    }
+    V2 uxa, uya, uza, uxb, uyb, uzb;
+    collide_mrt2<S::SHIFTED>(fa, a.tau0, a.csm18, uxa, uya, uza);
+    collide_mrt2<S::SHIFTED>(fb, a.tau0, a.csm18, uxb, uyb, uzb);
+    if (!valid) return;
+    const int c = o00 + x0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) S::st4(a.out[q] + c, make_float4(fa[q].x, fa[q].y, fb[q].x, fb[q].y));
+    if (STATS) {
+        const long long N = (long long)plane * nz;
+        *reinterpret_cast<float4 *>(a.ubuf + c) = make_float4(uxa.x, uxa.y, uxb.x, uxb.y);
+        *reinterpret_cast<float4 *>(a.ubuf + N + c) = make_float4(uya.x, uya.y, uyb.x, uyb.y);
+        *reinterpret_cast<float4 *>(a.ubuf + 2 * N + c) = make_float4(uza.x, uza.y, uzb.x, uzb.y);
+    }
+    if (a.check) {
+        const V2 ua = vfma(uxa, uxa, vfma(uya, uya, uza * uza));
+        const V2 ub = vfma(uxb, uxb, vfma(uyb, uyb, uzb * uzb));
+        if (!(ua.x < 0.09f) || !(ua.y < 0.09f) || !(ub.x < 0.09f) || !(ub.y < 0.09f))
+            atomicAdd(a.flags + 1, 1u);                  // also catches NaN
     }
 }
 

@@ -89,3 +89,22 @@ def test_half_storage_needs_half_the_lattice_bytes():
     assert sizes[1] == sizes[2]
     lat32, lat16 = 2 * 19 * 65536 * 4, 2 * 19 * 65536 * 2
     assert sizes[0] - sizes[1] == pytest.approx(lat32 - lat16, abs=1024)
+
+
+def test_step_kernel_selection_is_checked_on_the_host():
+    lib = _abi.lib()
+    rc, h = _create(nx=15)
+    assert rc == 0
+    assert lib.lbm_set_step_kernel(h, 7) == _abi.LBM_EINVAL
+    assert lib.lbm_set_step_kernel(h, -1) == _abi.LBM_EINVAL
+    assert lib.lbm_set_step_kernel(h, _abi.LBM_KERNEL_PAIR) == _abi.LBM_EINVAL      # nx odd
+    assert lib.lbm_set_step_kernel(h, _abi.LBM_KERNEL_STAGED) == _abi.LBM_EINVAL    # nx % 4 != 0
+    assert lib.lbm_set_step_kernel(h, _abi.LBM_KERNEL_CELL) == 0
+    k = ct.c_int(-1)
+    assert lib.lbm_get_step_kernel(h, ct.byref(k)) == 0 and k.value == _abi.LBM_KERNEL_CELL
+    assert lib.lbm_get_step_kernel(h, None) == _abi.LBM_EINVAL
+    lib.lbm_destroy(h)
+    rc, h = _create(nx=16)
+    assert lib.lbm_set_step_kernel(h, _abi.LBM_KERNEL_PAIR) == 0
+    assert lib.lbm_get_step_kernel(h, ct.byref(k)) == 0 and k.value == _abi.LBM_KERNEL_PAIR
+    lib.lbm_destroy(h)
