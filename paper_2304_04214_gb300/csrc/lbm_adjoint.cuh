@@ -520,18 +520,24 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     }
 }
 
-template <bool W>
-__device__ __noinline__ void adjoint_cell_wall(const AdjArgs &a, int i, int j, int k, int tx, float (*sh)[4]) {
-    adjoint_cell<true>(a, i, j, k, tx, sh);
-}
-
-__global__ void __launch_bounds__(128, 4) adjoint_kernel(const __grid_constant__ AdjArgs a) {
+// Rows 0, 1 (blockIdx.y = 0) and ny-2, ny-1 (blockIdx.y = 1): the wall cells
+// and their second cells, which exchange u_2 and its adjoint through shared
+// memory.  Launched beside the interior kernel: every pushed entry has one
+// writer (the outlet entries take atomics), so the two never write the same
+// word.
+__global__ void __launch_bounds__(128, 4) adjoint_wall_kernel(const __grid_constant__ AdjArgs a) {
     __shared__ float sh[128 / BY][4];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (blockIdx.y == 0 || blockIdx.y == gridDim.y - 1) adjoint_cell_wall<true>(a, i, j, k, threadIdx.x, sh);
-    else adjoint_cell<false>(a, i, j, k, threadIdx.x, sh);
+    const int j = blockIdx.y == 0 ? threadIdx.y : a.ny - 2 + threadIdx.y;
+    adjoint_cell<true>(a, i, j, blockIdx.z, threadIdx.x, sh);
+}
+
+// Rows 2 .. ny-3.  Latency-bound: five resident blocks per SM (a register
+// budget of 102) beat four without spills.
+__global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__ AdjArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 2 + blockIdx.y * BY + threadIdx.y;
+    adjoint_cell<false>(a, i, j, blockIdx.z, threadIdx.x, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -686,6 +692,23 @@ __global__ void __launch_bounds__(128) objective_kernel(const float *__restrict_
         __syncthreads();
     }
     if (tid == 0 && red[0][0] != 0.0) atomicAdd(acc, red[0][0]);
+}
+
+// J_R seeds from the window sums of objective_kernel / the step kernels, one
+// thread per row j: with <.> the mean over z and the window (cnt samples),
+// r_j = (<uv> - <u><v>) / u_ref^2 - R12(j) / u_ref^2 and J_R = sum_j r_j^2, so
+// dJ_R/du = 2 r_j (v - <v>) / (u_ref^2 cnt) and likewise for v:
+// coef[j] = 2 r_j / (u_ref^2 cnt), mean[j] = <u>, mean[ny + j] = <v>.
+__global__ void objective_seed_kernel(const double *__restrict__ acc, const double *__restrict__ R12,
+                                      float *__restrict__ coef, float *__restrict__ mean, int ny, double cnt,
+                                      double ur2) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ny) return;
+    const double mu = acc[1 + 3 * j] / cnt, mv = acc[2 + 3 * j] / cnt, muv = acc[3 + 3 * j] / cnt;
+    const double r = (muv - mu * mv) / ur2 - R12[j] / ur2;
+    coef[j] = (float)(2.0 * r / (ur2 * cnt));
+    mean[j] = (float)mu;
+    mean[ny + j] = (float)mv;
 }
 
 }  // namespace lbmk

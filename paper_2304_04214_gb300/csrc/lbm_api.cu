@@ -87,7 +87,7 @@ struct AdjointWork {
     float *vwin = nullptr, *luin = nullptr, *jr_coef = nullptr, *jr_mean = nullptr;
     float *dsq = nullptr, *aunit = nullptr, *dUR = nullptr;
     float4 *kphase = nullptr;
-    double *gtheta = nullptr, *objacc = nullptr;
+    double *gtheta = nullptr, *objacc = nullptr, *r12 = nullptr;
     float cell_scale = 0.f;
     bool have_lambda0 = false;
 };
@@ -142,6 +142,9 @@ struct lbm_handle {
     // forked from and joined back into the handle's stream every step
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // a second side stream for the STG work of lbm_adjoint_step
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_aux_fork = nullptr, ev_aux_join = nullptr;
     float *pin_stage = nullptr;            // pinned staging of U_R and amp*chol(R): 7*ny floats
     cudaEvent_t stage_ev = nullptr;        // last upload from the staging buffer
     // instrumentation
@@ -375,6 +378,7 @@ struct lbm_handle {
         adj.kphase = ar.take<float4>(N);
         adj.gtheta = ar.take<double>(4);
         adj.objacc = ar.take<double>(1 + 3 * (size_t)ny);
+        adj.r12 = ar.take<double>(ny);
         return (ar.off + 255) & ~size_t(255);
     }
 
@@ -466,6 +470,9 @@ struct StepIO {
     float *utau, *fw;
     const float *vprime;
     bool stats;
+    // objective sums accumulated by the step (pair and wall kernels; null: none)
+    double *obj = nullptr;
+    int obj_i0 = 0, obj_i1 = 0, obj_iR = -1;
 };
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime
@@ -596,10 +603,12 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
     a.csm18 = (float)(18.0 * std::sqrt(2.0) * h->opts.c_smag);
     a.y1_nu = (float)(0.5 / h->nu);
     a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
+    a.obj = io.obj; a.obj_i0 = io.obj_i0; a.obj_i1 = io.obj_i1; a.obj_iR = io.obj_iR;
     const int bxmax = lbmk::STEP_THREADS / lbmk::BY;
     const size_t slot = h->prof_on ? prof_slot(h) : 0;
     if (h->prof_on) cudaEventRecord(h->ev0[slot], h->stream);
-    const int kind = resolve_kind(h);
+    int kind = resolve_kind(h);
+    if (io.obj && kind != LBM_KERNEL_CELL) kind = LBM_KERNEL_PAIR;   // the kernel that sums the objective
     cudaError_t err = cudaSuccess;
     if (kind == LBM_KERNEL_STAGED || kind == LBM_KERNEL_PAIR || kind == LBM_KERNEL_QUAD) {
         // the wall rows on the side stream, the interior rows on the handle's
@@ -695,14 +704,14 @@ int one_step(lbm_handle *h) {
 }
 
 // STG field v' of steps t0 .. t0 + n - 1 into an explicit buffer
-void launch_stg_into(lbm_handle *h, float *out, long long t0, int n) {
+void launch_stg_into(lbm_handle *h, float *out, long long t0, int n, cudaStream_t st) {
     lbmk::StgArgs a;
     a.alpha = h->d_alpha; a.betaT = h->d_betaT; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
     a.sqsig = h->d_sqsig; a.amat = h->d_amat; a.UR = h->d_UR; a.out = out;
     a.t0 = t0; a.nsteps = n; a.apply_profile = 0;
     a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
     dim3 grid((h->nz + lbmk::STG_KZ - 1) / lbmk::STG_KZ, h->ny, (n + lbmk::STG_KT - 1) / lbmk::STG_KT);
-    lbmk::stg_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, h->stream>>>(a);
+    lbmk::stg_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, st>>>(a);
     h->launches += 1;
 }
 
@@ -725,23 +734,31 @@ void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lou
     a.csm18 = (float)(18.0 * std::sqrt(2.0) * h->opts.c_smag);
     a.y1_nu = (float)(0.5 / h->nu);
     a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
+    // wall rows and their second rows on the side stream, the rest on the
+    // handle's stream (disjoint writes), joined before anything that follows
     const int bx = 64;
-    dim3 block(bx, lbmk::BY), grid((h->nx + bx - 1) / bx, h->ny / lbmk::BY, h->nz);
-    lbmk::adjoint_kernel<<<grid, block, 0, h->stream>>>(a);
-    h->launches += 1;
+    const dim3 block(bx, lbmk::BY);
+    const int nbx = (h->nx + bx - 1) / bx;
+    cudaEventRecord(h->ev_fork, h->stream);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    lbmk::adjoint_wall_kernel<<<dim3(nbx, 2, h->nz), block, 0, h->side>>>(a);
+    cudaEventRecord(h->ev_join, h->side);
+    if (h->ny > 4) lbmk::adjoint_kernel<<<dim3(nbx, (h->ny - 4) / lbmk::BY, h->nz), block, 0, h->stream>>>(a);
+    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    h->launches += 2;
 }
 
 // theta gradient through the inlet velocity for nsteps steps from t0
-void launch_stg_adjoint(lbm_handle *h, long long t0, int nsteps) {
+void launch_stg_adjoint(lbm_handle *h, long long t0, int nsteps, const float *luin, cudaStream_t st) {
     if (!h->opts.inlet) return;
     lbmk::StgAdjArgs a;
     a.alpha = h->d_alpha; a.betaT = h->d_betaT; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
     a.sqsig = h->d_sqsig; a.dsq = h->adj.dsq; a.kphase = h->adj.kphase; a.aunit = h->adj.aunit;
-    a.dUR = h->adj.dUR; a.luin = h->adj.luin; a.gtheta = h->adj.gtheta;
+    a.dUR = h->adj.dUR; a.luin = luin; a.gtheta = h->adj.gtheta;
     a.amp = (float)h->theta[1]; a.cell_scale = h->adj.cell_scale;
     a.t0 = t0; a.nsteps = nsteps; a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
     dim3 grid((h->nz + lbmk::STG_KZ - 1) / lbmk::STG_KZ, h->ny, (nsteps + lbmk::STG_KT - 1) / lbmk::STG_KT);
-    lbmk::stg_adjoint_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, h->stream>>>(a);
+    lbmk::stg_adjoint_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, st>>>(a);
     h->launches += 1;
 }
 
@@ -845,7 +862,10 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
         cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_aux_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_aux_join, cudaEventDisableTiming) != cudaSuccess) {
         if (h->owns) cudaFree(h->mem);
         h->mem = nullptr;
         return cuda_fail(cudaGetLastError());
@@ -1248,8 +1268,19 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     const long long t0 = h->t;
     cudaStream_t st = h->stream;
     cudaError_t e;
-    // STG field of the window, accumulators
-    if (h->opts.inlet) launch_stg_into(h, A.vwin, t0, T);
+    // STG field of the window on the aux stream, beside the copies below
+    if (h->opts.inlet) {
+        if ((e = cudaEventRecord(h->ev_aux_fork, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->aux, h->ev_aux_fork, 0)) != cudaSuccess)
+            return cuda_fail(e);
+        launch_stg_into(h, A.vwin, t0, T, h->aux);
+        if ((e = cudaEventRecord(h->ev_aux_join, h->aux)) != cudaSuccess) return cuda_fail(e);
+    }
+    // prescribed R12 of the J_R target, accumulators
+    std::vector<double> r12(ny);
+    for (int j = 0; j < ny; ++j) r12[j] = h->prof_R[6 * (size_t)j + 3];
+    if ((e = cudaMemcpyAsync(A.r12, r12.data(), ny * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
     if ((e = cudaMemsetAsync(A.objacc, 0, (1 + 3 * (size_t)ny) * sizeof(double), st)) != cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaMemsetAsync(A.gtheta, 0, 4 * sizeof(double), st)) != cudaSuccess) return cuda_fail(e);
@@ -1259,12 +1290,20 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
         return cuda_fail(e);
     if ((e = cudaMemcpyAsync(A.ckpt, h->lat[h->cur], L * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return cuda_fail(e);
+    if (h->opts.inlet && (e = cudaStreamWaitEvent(st, h->ev_aux_join, 0)) != cudaSuccess) return cuda_fail(e);
     const int obj_blocks = ny + (2 * nz * (obj->i_tau1 - obj->i_tau0) + 127) / 128;
+    // the objective sums ride along in the step kernels, except in the
+    // one-cell kernel (nx odd), which leaves them to objective_kernel
+    const bool fused_obj = resolve_kind(h) != LBM_KERNEL_CELL;
     const void *cur = A.ckpt;
     int pp = 0;                                  // next lattice buffer of the ping-pong
+    // the states inside the last segment go straight to the segment slots,
+    // so that the reverse sweep starts without recomputing them
+    const int last_base = T - K;
     for (int n = 0; n < T; ++n) {
         void *out;
         if ((n + 1) % K == 0 && n + 1 < T) out = A.ckpt + (size_t)((n + 1) / K) * L;
+        else if (n + 1 > last_base && n + 1 < T) out = A.seg + (size_t)(n - last_base) * L;
         else { out = h->lat[pp]; pp ^= 1; }
         if (out == cur) { out = h->lat[pp]; pp ^= 1; }
         StepIO io;
@@ -1272,40 +1311,25 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
         io.utau_in = n == 0 ? A.ut_init : A.uthist + (size_t)(n - 1) * W;
         io.utau = A.uthist + (size_t)n * W;
         io.fw = h->d_fw; io.vprime = A.vwin + (size_t)n * I; io.stats = false;
+        if (fused_obj) { io.obj = A.objacc; io.obj_i0 = obj->i_tau0; io.obj_i1 = obj->i_tau1; io.obj_iR = obj->i_R; }
         if (cudaError_t le = launch_step_io(h, io)) return cuda_fail(le);
         h->t += 1;
         cur = out;
-        lbmk::objective_kernel<<<obj_blocks, 128, 0, st>>>((const float *)cur, h->d_fw, A.objacc, nx, ny, nz,
-                                                           obj->i_tau0, obj->i_tau1, obj->i_R);
-        h->launches += 1;
+        if (!fused_obj) {
+            lbmk::objective_kernel<<<obj_blocks, 128, 0, st>>>((const float *)cur, h->d_fw, A.objacc, nx, ny, nz,
+                                                               obj->i_tau0, obj->i_tau1, obj->i_R);
+            h->launches += 1;
+        }
     }
     h->cur = cur == h->lat[0] ? 0 : 1;          // s_T is in a lattice buffer
     if ((e = cudaMemcpyAsync(h->d_utau, A.uthist + (size_t)(T - 1) * W, W * 4, cudaMemcpyDeviceToDevice, st)) !=
         cudaSuccess) return cuda_fail(e);
-    // ---- objective on the host (FP64) and the J_R seeds ----
-    std::vector<double> acc(1 + 3 * (size_t)ny);
-    if ((e = cudaMemcpyAsync(acc.data(), A.objacc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
-        cudaSuccess) return cuda_fail(e);
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+    // ---- J_R seeds on the device (no host round trip between the sweeps) ----
     const double ur2 = h->utau_ref * h->utau_ref;
     const double nw = 2.0 * (obj->i_tau1 - obj->i_tau0) * nz;
-    const double Jt = nw > 0 ? acc[0] / (T * nw * ur2) : 0.0;
-    double JR = 0.0;
-    std::vector<float> coef(ny), mean(2 * (size_t)ny);
-    for (int j = 0; j < ny; ++j) {
-        const double cnt = (double)T * nz;
-        const double mu = acc[1 + 3 * j] / cnt, mv = acc[2 + 3 * j] / cnt, muv = acc[3 + 3 * j] / cnt;
-        const double r = (muv - mu * mv) / ur2 - h->prof_R[6 * (size_t)j + 3] / ur2;
-        JR += r * r;
-        coef[j] = (float)(2.0 * r / (ur2 * cnt));
-        mean[j] = (float)mu;
-        mean[ny + j] = (float)mv;
-    }
-    *J = Jt + JR;
-    if ((e = cudaMemcpyAsync(A.jr_coef, coef.data(), ny * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_fail(e);
-    if ((e = cudaMemcpyAsync(A.jr_mean, mean.data(), 2 * ny * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_fail(e);
+    lbmk::objective_seed_kernel<<<(ny + 63) / 64, 64, 0, st>>>(A.objacc, A.r12, A.jr_coef, A.jr_mean, ny,
+                                                               (double)T * nz, ur2);
+    h->launches += 1;
     const float jtau_w = nw > 0 ? (float)(1.0 / (T * nw * ur2)) : 0.0f;
     // ---- reverse: segments from the last, recompute from the checkpoint ----
     if ((e = cudaMemsetAsync(A.lamA, 0, L * 4, st)) != cudaSuccess) return cuda_fail(e);
@@ -1315,7 +1339,8 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     for (int sgm = T / K - 1; sgm >= 0; --sgm) {
         const int base = sgm * K;
         const float *prev = A.ckpt + (size_t)sgm * L;
-        for (int m = 1; m < K; ++m) {
+        // (the last segment's states are still in the slots from the forward pass)
+        for (int m = 1; m < K && sgm != T / K - 1; ++m) {
             const int n = base + m - 1;
             StepIO io;
             io.in = prev; io.out = A.seg + (size_t)(m - 1) * L;
@@ -1331,15 +1356,41 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
                            h->opts.inlet ? A.luin + (size_t)n * I : nullptr, true, obj, jtau_w);
             std::swap(lam, lout);
         }
+        // theta gradient through this segment's inlet velocities, beside the
+        // next segment's recomputation
+        if (h->opts.inlet) {
+            if ((e = cudaEventRecord(h->ev_aux_fork, st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(h->aux, h->ev_aux_fork, 0)) != cudaSuccess)
+                return cuda_fail(e);
+            launch_stg_adjoint(h, t0 + base, K, A.luin + (size_t)base * I, h->aux);
+        }
     }
     h->t = t_end;
     if (lam != A.lamA) std::swap(A.lamA, A.lamB);   // lambda_0 in lamA
-    launch_stg_adjoint(h, t0, T);
+    if (h->opts.inlet) {
+        if ((e = cudaEventRecord(h->ev_aux_join, h->aux)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, h->ev_aux_join, 0)) != cudaSuccess)
+            return cuda_fail(e);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    // ---- J (FP64, on the host) from the window sums, and dJ/dtheta ----
+    std::vector<double> acc(1 + 3 * (size_t)ny);
+    if ((e = cudaMemcpyAsync(acc.data(), A.objacc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemcpyAsync(dJ_dtheta, A.gtheta, 4 * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+    const double Jt = nw > 0 ? acc[0] / (T * nw * ur2) : 0.0;
+    double JR = 0.0;
+    for (int j = 0; j < ny; ++j) {
+        const double cnt = (double)T * nz;
+        const double mu = acc[1 + 3 * j] / cnt, mv = acc[2 + 3 * j] / cnt, muv = acc[3 + 3 * j] / cnt;
+        const double r = (muv - mu * mv) / ur2 - h->prof_R[6 * (size_t)j + 3] / ur2;
+        JR += r * r;
+    }
+    *J = Jt + JR;
     A.have_lambda0 = true;
-    return cuda_fail(cudaStreamSynchronize(st));
+    return LBM_OK;
 }
 
 int lbm_adjoint_state_gradient(lbm_handle *h, double *lambda0) {
@@ -1366,7 +1417,7 @@ int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, 
     const size_t L = 19 * (size_t)h->ncell, W = 2 * (size_t)h->nz * h->nx;
     cudaStream_t st = h->stream;
     cudaError_t e;
-    if (h->opts.inlet) launch_stg_into(h, A.vwin, h->t, 1);
+    if (h->opts.inlet) launch_stg_into(h, A.vwin, h->t, 1, h->stream);
     if ((e = cudaMemsetAsync(A.gtheta, 0, 4 * sizeof(double), st)) != cudaSuccess) return cuda_fail(e);
     // forward step into scratch for this step's u_tau (the state stays)
     if ((e = cudaMemcpyAsync(A.ut_scr, h->d_utau, W * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
@@ -1382,7 +1433,7 @@ int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, 
     if ((e = cudaMemsetAsync(A.lamB, 0, L * 4, st)) != cudaSuccess) return cuda_fail(e);
     launch_adjoint(h, (const float *)h->lat[h->cur], A.lamA, A.lamB, A.ut_scr, A.vwin,
                    h->opts.inlet ? A.luin : nullptr, false, nullptr, 0.0f);
-    launch_stg_adjoint(h, h->t, 1);
+    launch_stg_adjoint(h, h->t, 1, h->adj.luin, h->stream);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemcpyAsync(buf.data(), A.lamB, L * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e);
@@ -1405,6 +1456,9 @@ void lbm_destroy(lbm_handle *h) {
     if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) { cudaStreamSynchronize(h->aux); cudaStreamDestroy(h->aux); }
+    if (h->ev_aux_fork) cudaEventDestroy(h->ev_aux_fork);
+    if (h->ev_aux_join) cudaEventDestroy(h->ev_aux_join);
     delete h;
 }
 

@@ -527,6 +527,10 @@ struct StepArgs {
     int reverse;                             // traverse the lattice backwards this step
     float tau0, csm18;                       // tau0, 18 sqrt2 C_smag
     float y1_nu, kappa, B;                   // y1 / nu, Reichardt constants
+    // objective accumulators (null: none): [0] sum of tau_w over the wall cells
+    // with obj_i0 <= i < obj_i1; [1 + 3j ..] sums over z of u, v, u v at i = obj_iR
+    double *obj;
+    int obj_i0, obj_i1, obj_iR;
 };
 
 constexpr int BY = 2;  // rows per block: (0,1) and (ny-2,ny-1) share a block
@@ -841,6 +845,18 @@ __global__ void __launch_bounds__(WALL_THREADS) wall_kernel(const __grid_constan
     float ux, uy, uz;
     if (a.wall_model) collide_mrt<S::SHIFTED, true>(f, P, Fx, 0.0f, Fz, a.tau0, a.csm18, ux, uy, uz);
     else collide_mrt<S::SHIFTED, false>(f, P, 0.0f, 0.0f, 0.0f, a.tau0, a.csm18, ux, uy, uz);
+    if (a.obj) {                                     // objective sums (launch-uniform branch)
+        float tw = 0.0f;
+        if (valid && i >= a.obj_i0 && i < a.obj_i1) tw = sqrtf(Fx * Fx + Fz * Fz);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tw += __shfl_xor_sync(0xffffffffu, tw, o);
+        if ((threadIdx.x & 31) == 0 && tw != 0.0f) atomicAdd(a.obj, (double)tw);
+        if (valid && i == a.obj_iR) {
+            atomicAdd(a.obj + 1 + 3 * j, (double)ux);
+            atomicAdd(a.obj + 2 + 3 * j, (double)uy);
+            atomicAdd(a.obj + 3 + 3 * j, (double)(ux * uy));
+        }
+    }
     if (valid) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
 }
 
@@ -892,6 +908,12 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, Step2Blocks<S>::value) step2
     V2 ux, uy, uz;
     collide_mrt2<S::SHIFTED>(f, a.tau0, a.csm18, ux, uy, uz);
     if (!valid) return;
+    if (a.obj && (i0 == a.obj_iR || i0 + 1 == a.obj_iR)) {     // J_R sums at x = i_R
+        const float u = i0 == a.obj_iR ? ux.x : ux.y, v = i0 == a.obj_iR ? uy.x : uy.y;
+        atomicAdd(a.obj + 1 + 3 * j, (double)u);
+        atomicAdd(a.obj + 2 + 3 * j, (double)v);
+        atomicAdd(a.obj + 3 + 3 * j, (double)(u * v));
+    }
     const int c = (k * ny + j) * nx + ic;
 #pragma unroll
     for (int q = 0; q < 19; ++q) S::st2(a.out[q] + c, f[q]);
