@@ -619,7 +619,7 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
         if ((err = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess ||
             (err = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess)
             return err;
-        const dim3 wgrid((h->nx + lbmk::WALL_THREADS - 1) / lbmk::WALL_THREADS, 2, h->nz);
+        const dim3 wgrid((h->nx + lbmk::WALL_THREADS - 1) / lbmk::WALL_THREADS, h->nz);
         if (io.stats) lbmk::wall_kernel<S, true><<<wgrid, lbmk::WALL_THREADS, 0, h->side>>>(a);
         else lbmk::wall_kernel<S, false><<<wgrid, lbmk::WALL_THREADS, 0, h->side>>>(a);
         if ((err = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return err;

@@ -127,14 +127,16 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // Reichardt law, Sec. 2.3 eq:reichard with the textbook coefficients
 // (1/kappa, kappa, B), and its derivative in y+.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float reichardt_f(float yp, float kap, float B) {
-    return log1pf(kap * yp) / kap + B * (1.0f - expf(-yp * (1.0f / 11.0f))
-                                         - yp * (1.0f / 11.0f) * expf(-yp * (1.0f / 3.0f)));
-}
-__device__ __forceinline__ float reichardt_dy_f(float yp, float kap, float B) {
-    const float e3 = expf(-yp * (1.0f / 3.0f));
-    return 1.0f / (1.0f + kap * yp)
-         + B * (expf(-yp * (1.0f / 11.0f)) * (1.0f / 11.0f) - e3 * (1.0f / 11.0f) + yp * (1.0f / 33.0f) * e3);
+// The law and its derivative together, with the fast exponential and
+// logarithm (MUFU-based intrinsics): at the y+ of a first cell their relative
+// errors (~1e-6 in e^{-y+/3}) enter u+ below 1e-7, under FP32 rounding of the
+// Newton residual.  The two exponentials are shared by the law and its slope.
+__device__ __forceinline__ void reichardt_fast(float yp, float kap, float B, float &up, float &dup) {
+    const float e11 = __expf(yp * (-1.0f / 11.0f)), e3 = __expf(yp * (-1.0f / 3.0f));
+    const float ky = fmaf(kap, yp, 1.0f);
+    const float ik = rcp_approx(kap);
+    up = __logf(ky) * ik + B * (1.0f - e11 - yp * (1.0f / 11.0f) * e3);
+    dup = rcp_approx(ky) + B * ((e11 - e3) * (1.0f / 11.0f) + yp * (1.0f / 33.0f) * e3);
 }
 __device__ __forceinline__ double reichardt_d(double yp, double kap, double B) {
     return log1p(kap * yp) / kap + B * (1.0 - exp(-yp / 11.0) - yp / 11.0 * exp(-yp / 3.0));
@@ -156,9 +158,10 @@ __device__ __forceinline__ float solve_utau_dev(float uhat, float y1_nu, float k
     float u = guess > 0.0f ? guess : 1e-3f;
     for (int it = 0; it < 12; ++it) {
         const float yp = y1_nu * u;
-        const float up = reichardt_f(yp, kap, B);
+        float up, dup;
+        reichardt_fast(yp, kap, B, up, dup);
         const float r = u * up - uhat;
-        const float dr = up + yp * reichardt_dy_f(yp, kap, B);
+        const float dr = up + yp * dup;
         const float du = r * rcp_approx(dr);
         float un = u - du;
         if (!(un > 0.0f)) un = 0.5f * u;
@@ -770,20 +773,18 @@ __device__ __forceinline__ void inlet_velocity(const StepArgs<S> &a, int j, int 
     vz = m[3] * vp[0] + m[4] * vp[1] + m[5] * vp[2];
 }
 
-// The wall rows j = 0 and j = ny - 1 of the step, one cell per thread: block
-// = 128 x-cells of one wall row (blockIdx.y = 0 bottom, 1 top) and plane
-// blockIdx.z.  Launched beside the interior kernel (the rows are disjoint).
-// The Newton solve makes these threads latency-bound, so each does one cell:
-// both sets of pulled populations (its own, mirrored at the wall, and the
-// second cell's for u_2) are loaded up front, then the wall model and the
-// scalar collision with the wall force.
+// The wall rows j = 0 and j = ny - 1 of the step: one thread per (x, z) takes
+// the bottom and the top wall cell as the two lanes of the packed collision
+// (.x bottom, .y top).  Launched beside the interior kernel (the rows are
+// disjoint).  Per lane: the pulled populations, mirrored at the wall; u_2 of
+// the second cell (row 1 / ny - 2) summed from its pulled populations; the
+// regularized inlet at x = 0; the wall model (Sec. 2.3, Algorithm 1 steps
+// 9-14) with a scalar Newton solve; then the packed collision with the force.
 template <class S, bool STATS>
 __global__ void __launch_bounds__(WALL_THREADS) wall_kernel(const __grid_constant__ StepArgs<S> a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool bot = blockIdx.y == 0;
-    const int j = bot ? 0 : ny - 1, j2 = bot ? 1 : ny - 2, w = bot ? 0 : 1;
-    const int k = blockIdx.z;
+    const int k = blockIdx.y;
     const bool valid = i < nx;
     const int ic = valid ? i : nx - 1;
     int xm = ic - 1, xp = ic + 1;                    // sources for c_x = +1 / -1
@@ -792,72 +793,123 @@ __global__ void __launch_bounds__(WALL_THREADS) wall_kernel(const __grid_constan
     const int plane = nx * ny;
     const int ozm = k == 0 ? (nz - 1) * plane : -plane;       // source plane for c_z = +1
     const int ozp = k == nz - 1 ? -(nz - 1) * plane : plane;  // source plane for c_z = -1
-    const int o00 = (k * ny + j) * nx, o2 = (k * ny + j2) * nx;
-    float f[19], g[19];
-    load_pulled<S, true>(a, f, o00, ozm, ozp, bot ? 0 : -nx, bot ? nx : 0, ic, xm, xp, bot, !bot);
-    if (a.wall_model) load_pulled<S, false>(a, g, o2, ozm, ozp, -nx, nx, ic, xm, xp, false, false);
-    const bool inlet_cell = a.inlet && i == 0;
-    if (inlet_cell) inlet_rebuild<S>(a, f, j, k);
-    Pairs P;
-    make_pairs<S::SHIFTED>(f, P);
-    float Fx = 0.0f, Fz = 0.0f;
-    if (a.wall_model) {
-        // u_2 of the second cell: tangential momentum over density (at the
-        // inlet: u_in, the velocity its regularized rebuild gives)
-        float u2x, u2z;
-        if (inlet_cell) {
-            float vy;
-            inlet_velocity<S>(a, j2, k, u2x, vy, u2z);
-        } else {
-            Pairs P2;
-            make_pairs<S::SHIFTED>(g, P2);
-            const float ir2 = rcp_approx(1.0f + P2.drho);
-            u2x = P2.jx * ir2; u2z = P2.jz * ir2;
-        }
-        // eq:base: e_x from the tangential part of u_2 (the wall normal is y);
-        // eq:uhat with the first-cell velocity; Newton for u_tau; tau_w = rho u_tau^2
-        const float tn = sqrtf(u2x * u2x + u2z * u2z);
-        const size_t iu = ((size_t)w * nz + k) * nx + ic;
-        float ut_new = a.utau_in[iu];
-        if (tn >= 1e-12f) {
-            const float itn = rcp_approx(tn);
-            const float ex = u2x * itn, ez = u2z * itn;
-            const float rho = 1.0f + P.drho;
-            const float uhat = (P.jx * ex + P.jz * ez) * rcp_approx(rho);
-            const float sg = uhat < 0.0f ? -1.0f : 1.0f;
-            const float ua = fabsf(uhat);
-            float ut = 0.0f;
-            if (ua > 0.0f && valid) {
-                bool ok;
-                ut = solve_utau_dev(ua, a.y1_nu, a.kappa, a.B, ut_new, &ok);
-                if (!ok) atomicAdd(a.flags, 1u);
-            }
-            ut_new = ut;
-            const float tw = rho * ut * ut * sg;          // eq:force_wm with A = 1
-            Fx = -tw * ex; Fz = -tw * ez;
-        }
-        if (valid) {
-            a.utau[iu] = ut_new;
-            float *fwp = a.fw + (((size_t)w * nz + k) * nx + i) * 3;
-            fwp[0] = Fx; fwp[1] = 0.0f; fwp[2] = Fz;
+    const int ob = k * plane, ot = ob + (ny - 1) * nx;        // rows 0 and ny - 1
+    V2 f[19];
+    V2 r2 = vdup(0.0f), jx2 = vdup(0.0f), jz2 = vdup(0.0f);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const int oz = CZ(q) > 0 ? ozm : (CZ(q) < 0 ? ozp : 0);
+        const int x = CX(q) > 0 ? xm : (CX(q) < 0 ? xp : ic);
+        // bottom: c_y = +1 comes through the wall (mirrored, same row); top: c_y = -1
+        const int pb = CY(q) > 0 ? mirror_y(q) : q, pt = CY(q) < 0 ? mirror_y(q) : q;
+        const int rb = CY(q) < 0 ? nx : 0, rt = CY(q) > 0 ? -nx : 0;
+        f[q] = make_float2(S::ld(a.in[pb] + ob + rb + oz + x), S::ld(a.in[pt] + ot + rt + oz + x));
+        if (a.wall_model) {                          // second cells: rows 1 and ny - 2
+            const int ry = -CY(q) * nx;
+            const V2 g = make_float2(S::ld(a.in[q] + ob + nx + ry + oz + x),
+                                     S::ld(a.in[q] + ot - nx + ry + oz + x));
+            r2 = r2 + g;
+            if (CX(q) > 0) jx2 = jx2 + g;
+            if (CX(q) < 0) jx2 = jx2 - g;
+            if (CZ(q) > 0) jz2 = jz2 + g;
+            if (CZ(q) < 0) jz2 = jz2 - g;
         }
     }
-    float ux, uy, uz;
-    if (a.wall_model) collide_mrt<S::SHIFTED, true>(f, P, Fx, 0.0f, Fz, a.tau0, a.csm18, ux, uy, uz);
-    else collide_mrt<S::SHIFTED, false>(f, P, 0.0f, 0.0f, 0.0f, a.tau0, a.csm18, ux, uy, uz);
+    const bool inlet_cell = a.inlet && i == 0;
+    if (inlet_cell) {
+        float fl[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) fl[q] = f[q].x;
+        inlet_rebuild<S>(a, fl, 0, k);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) { f[q].x = fl[q]; fl[q] = f[q].y; }
+        inlet_rebuild<S>(a, fl, ny - 1, k);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q].y = fl[q];
+    }
+    Pairs2 P;
+    make_pairs2<S::SHIFTED>(f, P);
+    V2 Fx = vdup(0.0f), Fz = vdup(0.0f);
+    if (a.wall_model) {
+        // u_2 of the second cells: tangential momentum over density (at the
+        // inlet: u_in, the velocity their regularized rebuild gives)
+        if (S::SHIFTED) r2 = r2 + vdup(1.0f);
+        const V2 ir2 = vrcp(r2);
+        float u2[2][2] = {{jx2.x * ir2.x, jz2.x * ir2.x}, {jx2.y * ir2.y, jz2.y * ir2.y}};
+        if (inlet_cell) {
+            float vy;
+            inlet_velocity<S>(a, 1, k, u2[0][0], vy, u2[0][1]);
+            inlet_velocity<S>(a, ny - 2, k, u2[1][0], vy, u2[1][1]);
+        }
+        const float rw[2] = {P.rho.x, P.rho.y}, jxw[2] = {P.jx.x, P.jx.y}, jzw[2] = {P.jz.x, P.jz.y};
+        float Fo[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            // eq:base: e_x from the tangential part of u_2 (the wall normal is y);
+            // eq:uhat with the first-cell velocity; Newton for u_tau; tau_w = rho u_tau^2
+            const float u2x = u2[w][0], u2z = u2[w][1];
+            const float tn = sqrtf(u2x * u2x + u2z * u2z);
+            const size_t iu = ((size_t)w * nz + k) * nx + ic;
+            float ut_new = a.utau_in[iu];
+            if (tn >= 1e-12f) {
+                const float itn = rcp_approx(tn);
+                const float ex = u2x * itn, ez = u2z * itn;
+                const float uhat = (jxw[w] * ex + jzw[w] * ez) * rcp_approx(rw[w]);
+                const float sg = uhat < 0.0f ? -1.0f : 1.0f;
+                const float ua = fabsf(uhat);
+                float ut = 0.0f;
+                if (ua > 0.0f && valid) {
+                    bool ok;
+                    ut = solve_utau_dev(ua, a.y1_nu, a.kappa, a.B, ut_new, &ok);
+                    if (!ok) atomicAdd(a.flags, 1u);
+                }
+                ut_new = ut;
+                const float tw = rw[w] * ut * ut * sg;       // eq:force_wm with A = 1
+                Fo[w][0] = -tw * ex; Fo[w][1] = -tw * ez;
+            }
+            if (valid) {
+                a.utau[iu] = ut_new;
+                float *fwp = a.fw + iu * 3;
+                fwp[0] = Fo[w][0]; fwp[1] = 0.0f; fwp[2] = Fo[w][1];
+            }
+        }
+        Fx = make_float2(Fo[0][0], Fo[1][0]);
+        Fz = make_float2(Fo[0][1], Fo[1][1]);
+    }
+    V2 ux, uy, uz;
+    if (a.wall_model) collide_pairs2<S::SHIFTED, true>(P, f, Fx, Fz, a.tau0, a.csm18, ux, uy, uz);
+    else collide_pairs2<S::SHIFTED, false>(P, f, Fx, Fz, a.tau0, a.csm18, ux, uy, uz);
     if (a.obj) {                                     // objective sums (launch-uniform branch)
         float tw = 0.0f;
-        if (valid && i >= a.obj_i0 && i < a.obj_i1) tw = sqrtf(Fx * Fx + Fz * Fz);
+        if (valid && i >= a.obj_i0 && i < a.obj_i1)
+            tw = sqrtf(Fx.x * Fx.x + Fz.x * Fz.x) + sqrtf(Fx.y * Fx.y + Fz.y * Fz.y);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tw += __shfl_xor_sync(0xffffffffu, tw, o);
         if ((threadIdx.x & 31) == 0 && tw != 0.0f) atomicAdd(a.obj, (double)tw);
         if (valid && i == a.obj_iR) {
-            atomicAdd(a.obj + 1 + 3 * j, (double)ux);
-            atomicAdd(a.obj + 2 + 3 * j, (double)uy);
-            atomicAdd(a.obj + 3 + 3 * j, (double)(ux * uy));
+            atomicAdd(a.obj + 1, (double)ux.x);
+            atomicAdd(a.obj + 2, (double)uy.x);
+            atomicAdd(a.obj + 3, (double)(ux.x * uy.x));
+            atomicAdd(a.obj + 1 + 3 * (ny - 1), (double)ux.y);
+            atomicAdd(a.obj + 2 + 3 * (ny - 1), (double)uy.y);
+            atomicAdd(a.obj + 3 + 3 * (ny - 1), (double)(ux.y * uy.y));
         }
     }
-    if (valid) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
+    if (!valid) return;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        S::st(a.out[q] + ob + i, f[q].x);
+        S::st(a.out[q] + ot + i, f[q].y);
+    }
+    if (STATS) {
+        const long long N = (long long)plane * nz;
+        a.ubuf[ob + i] = ux.x; a.ubuf[N + ob + i] = uy.x; a.ubuf[2 * N + ob + i] = uz.x;
+        a.ubuf[ot + i] = ux.y; a.ubuf[N + ot + i] = uy.y; a.ubuf[2 * N + ot + i] = uz.y;
+    }
+    if (a.check) {
+        const V2 uu = vfma(ux, ux, vfma(uy, uy, uz * uz));
+        if (!(uu.x < 0.09f) || !(uu.y < 0.09f)) atomicAdd(a.flags + 1, 1u);   // also catches NaN
+    }
 }
 
 // Interior rows 1 .. ny - 2, two x-adjacent cells (i, i+1), i even, per
