@@ -1,7 +1,7 @@
 """Long-run statistics of the CUDA path against the FP64 oracle: the
 64x32x32, Re_tau = 1000, N = 100 channel run for 4000 steps (about three
 flow-through times at U_b = 0.05) with the FP64 statistics accumulated every
-step, reduced to the profiles the method is judged by -- mean velocity U(y)
+step, reduced to the profiles that characterize the channel -- mean velocity U(y)
 and the Reynolds stresses <u'u'>, <v'v'>, <w'w'>, <u'v'> -- averaged over z,
 the samples and the downstream three quarters of the channel.
 
