@@ -201,6 +201,15 @@ int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R);
  * averaged over z: host out[w*nx + i], w = 0 bottom, 1 top.  Synchronizes. */
 int lbm_wall_shear(lbm_handle *h, double *out);
 
+/* The same reduction enqueued without synchronizing: out (2*nx doubles,
+ * owned by the caller, pinned host memory for the copy to be asynchronous)
+ * holds the result once the handle's stream has passed this point (after
+ * lbm_sync, a stream synchronize, or an event recorded after this call).
+ * Successive calls are stream-ordered, so two output buffers used in turn let
+ * a coupling loop read step n while step n + 1 runs.  Errors: LBM_EINVAL,
+ * LBM_ESTATE before lbm_bind_memory, LBM_ECUDA. */
+int lbm_wall_shear_async(lbm_handle *h, double *out);
+
 /* Wall shear for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this is a property of the library, not of the method.)
  *

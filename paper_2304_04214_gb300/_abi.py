@@ -72,6 +72,7 @@ PROTOTYPES = {
     "lbm_set_inlet_profile": (ct.c_int, [_h, _dp, _dp]),
     "lbm_get_inlet_profile": (ct.c_int, [_h, _dp, _dp]),
     "lbm_wall_shear": (ct.c_int, [_h, _dp]),
+    "lbm_wall_shear_async": (ct.c_int, [_h, _dp]),
     "lbm_wall_shear_noalloc": (ct.c_int, [_h, _dp]),
     "lbm_profile_enable": (ct.c_int, [_h, ct.c_int]),
     "lbm_profile_read": (ct.c_int, [_h, _dp, ct.POINTER(ct.c_long), ct.POINTER(ct.c_long)]),

@@ -148,6 +148,21 @@ class LBMChannel:
         _abi.check(self.lib.lbm_get_constants(self.h, _dptr(o)), "lbm_get_constants")
         return dict(delta=o[0], utau_ref=o[1], nu=o[2], tau0=o[3], ubp=o[4], maxl=o[5])
 
+    def wall_shear(self):
+        """z-averaged tau_w of the last step, (2, nx): bottom, top."""
+        out = np.empty(2 * self.nx)
+        _abi.check(self.lib.lbm_wall_shear(self.h, _dptr(out)), "lbm_wall_shear")
+        return out.reshape(2, self.nx)
+
+    def wall_shear_async(self, out):
+        """Enqueue the same reduction into `out` (a pinned float64 torch tensor
+        of 2 * nx values) without synchronizing; it holds the result once the
+        stream has passed this point."""
+        if out.dtype != self._torch.float64 or out.numel() != 2 * self.nx or out.is_cuda:
+            raise ValueError("out must be a host float64 tensor of 2 * nx values")
+        _abi.check(self.lib.lbm_wall_shear_async(self.h, ct.cast(out.data_ptr(), ct.POINTER(ct.c_double))),
+                   "lbm_wall_shear_async")
+
     def stats(self):
         s = np.empty((self.ny, self.nx, 7))
         ut = np.empty((2, self.nx))

@@ -1132,7 +1132,7 @@ int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R) {
     return LBM_OK;
 }
 
-int lbm_wall_shear(lbm_handle *h, double *out) {
+int lbm_wall_shear_async(lbm_handle *h, double *out) {
     if (!h || !out) return LBM_EINVAL;
     if (!h->bound) return LBM_ESTATE;
     const int n = 2 * h->nx;
@@ -1140,8 +1140,12 @@ int lbm_wall_shear(lbm_handle *h, double *out) {
     h->launches += 1;
     cudaError_t e;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-    if ((e = cudaMemcpyAsync(out, h->d_tw, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
-        return cuda_fail(e);
+    return cuda_fail(cudaMemcpyAsync(out, h->d_tw, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+}
+
+int lbm_wall_shear(lbm_handle *h, double *out) {
+    const int rc = lbm_wall_shear_async(h, out);
+    if (rc) return rc;
     return cuda_fail(cudaStreamSynchronize(h->stream));
 }
 

@@ -166,3 +166,29 @@ def test_divergence_is_reported():
         g.sync()
     assert e.value.code == _abi.LBM_EDIVERGED
     g.sync()              # the flag is cleared once reported
+
+
+def test_async_wall_shear_matches_the_synchronous_call():
+    """lbm_wall_shear_async into two pinned buffers in turn gives, step by
+    step, what lbm_wall_shear returns; both match the oracle's tau_w."""
+    import torch
+    o, g = make_pair(64, 16, 8, n_modes=16, seed=9)
+    bufs = [torch.empty(2 * 64, dtype=torch.float64).pin_memory() for _ in range(2)]
+    outs = []
+    for n in range(4):
+        g.step(1)
+        g.wall_shear_async(bufs[n % 2])
+        if n >= 1:
+            g.sync()
+            outs.append(bufs[(n - 1) % 2].numpy().copy())
+    g.sync()
+    outs.append(bufs[3 % 2].numpy().copy())
+    assert len(outs) == 4 and all(np.all(np.isfinite(x)) for x in outs)
+    ref = g.wall_shear().reshape(-1)
+    assert np.array_equal(outs[-1], ref)
+    o.step(4)
+    rho, _ = o.fields()
+    ut = o.utau()                                   # (2, nz, nx)
+    # tau_w = rho u_tau^2 of the wall cells, z-averaged
+    tw = np.stack([(rho[:, 0, :] * ut[0] ** 2).mean(axis=0), (rho[:, -1, :] * ut[1] ** 2).mean(axis=0)])
+    assert np.max(np.abs(ref - tw.reshape(-1))) < 1e-4 * np.max(tw)
