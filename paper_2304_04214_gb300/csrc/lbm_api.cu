@@ -170,8 +170,8 @@ struct lbm_handle {
         d_st_utau = ar.take<double>(2 * (size_t)nx);
         d_tw = ar.take<double>(2 * (size_t)nx);
         d_flags = ar.take<unsigned>(4);
-        d_UR = ar.take<float>(ny);
-        d_amat = ar.take<float>(6 * (size_t)ny);
+        d_UR = ar.take<float>(7 * (size_t)ny);    // U_R[ny], then amp * chol(R)[ny][6]
+        d_amat = d_UR + ny;
         d_sqsig = ar.take<float4>((size_t)ny * N);
         d_alpha = ar.take<uint32_t>((size_t)ny * N);
         d_betaT = ar.take<uint32_t>((size_t)nz * N);
@@ -1117,10 +1117,8 @@ int lbm_set_inlet_profile(lbm_handle *h, const double *U, const double *R) {
     if ((e = cudaEventSynchronize(h->stage_ev)) != cudaSuccess) return cuda_fail(e);
     std::copy(h->UR.begin(), h->UR.end(), h->pin_stage);
     std::copy(h->amat.begin(), h->amat.end(), h->pin_stage + h->ny);
-    // d_UR and d_amat are adjacent in the arena only up to alignment: two copies
-    if ((e = cudaMemcpyAsync(h->d_UR, h->pin_stage, h->ny * 4, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
-        return cuda_fail(e);
-    if ((e = cudaMemcpyAsync(h->d_amat, h->pin_stage + h->ny, 6 * h->ny * 4, cudaMemcpyHostToDevice,
+    // d_UR and d_amat are one block of 7 ny floats: one copy
+    if ((e = cudaMemcpyAsync(h->d_UR, h->pin_stage, 7 * (size_t)h->ny * 4, cudaMemcpyHostToDevice,
                              h->stream)) != cudaSuccess) return cuda_fail(e);
     return cuda_fail(cudaEventRecord(h->stage_ev, h->stream));
 }
@@ -1132,11 +1130,22 @@ int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R) {
     return LBM_OK;
 }
 
+}  // extern "C"
+
+// z-averaged wall shear of the last step into device memory out[2 * nx]
+// (every entry written).
+static void launch_wall_shear(lbm_handle *h, double *out) {
+    const dim3 grid((h->nx + lbmk::WS_X - 1) / lbmk::WS_X, 2), block(lbmk::WS_X, lbmk::WS_Z);
+    lbmk::wall_shear_kernel<<<grid, block, 0, h->stream>>>(h->d_fw, out, h->nx, h->nz);
+}
+
+extern "C" {
+
 int lbm_wall_shear_async(lbm_handle *h, double *out) {
     if (!h || !out) return LBM_EINVAL;
     if (!h->bound) return LBM_ESTATE;
     const int n = 2 * h->nx;
-    lbmk::wall_shear_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(h->d_fw, h->d_tw, h->nx, h->nz);
+    launch_wall_shear(h, h->d_tw);
     h->launches += 1;
     cudaError_t e;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
@@ -1186,7 +1195,7 @@ int lbm_wall_shear_noalloc(lbm_handle *h, double *out) {
     }
     const int n = 2 * h->nx;
     // every entry read below is written by this launch first
-    lbmk::wall_shear_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(h->d_fw, scratch, h->nx, h->nz);
+    launch_wall_shear(h, scratch);
     h->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemcpyAsync(out, scratch, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)

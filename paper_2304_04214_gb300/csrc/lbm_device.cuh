@@ -1220,17 +1220,29 @@ __global__ void __launch_bounds__(ST_COLS * ST_CHUNKS) stats_kernel(
 }
 
 // tau_w = |F_w| (= rho u_tau^2) averaged over z, per wall and x
-__global__ void wall_shear_kernel(const float *fw, double *out, int nx, int nz) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * nx) return;
-    const int w = t / nx, i = t % nx;
+// z-average of |F_w| (= tau_w) per wall and x: a block takes 32 x-columns
+// of one wall, its 16 thread rows split z, and their FP32 partial sums are
+// added in shared memory.
+constexpr int WS_X = 32, WS_Z = 16;
+__global__ void __launch_bounds__(WS_X * WS_Z) wall_shear_kernel(const float *fw, double *out, int nx, int nz) {
+    __shared__ float part[WS_Z][WS_X];
+    const int i = blockIdx.x * WS_X + threadIdx.x, w = blockIdx.y;
     float s = 0.0f;
-#pragma unroll 4
-    for (int k = 0; k < nz; ++k) {
-        const float *F = fw + (((size_t)w * nz + k) * nx + i) * 3;
-        s += sqrtf(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    if (i < nx) {
+#pragma unroll 8
+        for (int k = threadIdx.y; k < nz; k += WS_Z) {
+            const float *F = fw + (((size_t)w * nz + k) * nx + i) * 3;
+            s += sqrtf(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+        }
     }
-    out[t] = (double)s / nz;
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && i < nx) {
+        float t = 0.0f;
+#pragma unroll
+        for (int g = 0; g < WS_Z; ++g) t += part[g][threadIdx.x];
+        out[(size_t)w * nx + i] = (double)t / nz;
+    }
 }
 
 }  // namespace lbmk
