@@ -1,0 +1,119 @@
+"""Channel statistics in the form the paper reports them (Sec. 4): mean
+velocity and Reynolds-stress profiles along the channel in wall units, the
+friction velocity along both walls, and the adaptation length -- the distance
+from the inlet after which a quantity stays within a tolerance of its
+developed value.  Host post-processing of the FP64 sums that lbm_stats
+returns; the channel itself runs in the CUDA library.
+
+    python -m paper_2304_04214_gb300.analysis --re-tau 1000 --lbu 40
+
+runs the paper's set-up (Sec. 4.1: a 20 delta x 2 delta x 1.6 delta channel
+with H = 2 delta resolved by 20, 40 or 60 cells, 10 domain-through times,
+statistics after 2) and prints one JSON line.
+"""
+import argparse
+import json
+
+import numpy as np
+
+
+def profiles(sums, utau_sums, n_samples, nz):
+    """Means over z and samples from lbm_stats' sums.
+
+    sums: (ny, nx, 7) sums of (u, v, w, uu, vv, ww, uv); utau_sums: (2, nx).
+    Returns U, V, W (ny, nx), the centred second moments uu, vv, ww, uv
+    (ny, nx) and utau (2, nx)."""
+    m = np.asarray(sums, dtype=np.float64) / (n_samples * nz)
+    U, V, W = m[..., 0], m[..., 1], m[..., 2]
+    out = dict(U=U, V=V, W=W, uu=m[..., 3] - U * U, vv=m[..., 4] - V * V, ww=m[..., 5] - W * W,
+               uv=m[..., 6] - U * V)
+    out["utau"] = np.asarray(utau_sums, dtype=np.float64).reshape(2, -1) / (n_samples * nz)
+    return out
+
+
+def shear_stress_peak(uv, u_ref):
+    """Peak of the Reynolds shear stress -<u'v'>+ along x: the lower half as
+    is, the upper half with its sign flipped (the stress changes sign at the
+    centre line), averaged, then the maximum over y.  uv: (ny, nx)."""
+    ny = uv.shape[0]
+    h = ny // 2
+    lower = -uv[:h]
+    upper = uv[ny - 1:ny - 1 - h:-1]          # mirrored, row 0 = the wall row
+    return 0.5 * (lower + upper).max(axis=0) / (u_ref * u_ref)
+
+
+def adaptation_length(q, x, ref, tol):
+    """Smallest x0 with |q(x) / q_ref - 1| <= tol for every x0 <= x <= ref[1],
+    q_ref the mean of q over ref[0] <= x <= ref[1]; None if no such x0 exists
+    before ref[0]."""
+    q = np.asarray(q, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    sel = (x >= ref[0]) & (x <= ref[1])
+    q_ref = q[sel].mean()
+    ok = np.abs(q / q_ref - 1.0) <= tol
+    last = np.nonzero(x <= ref[1])[0][-1]
+    bad = np.nonzero(~ok[:last + 1])[0]
+    x0 = x[0] if bad.size == 0 else (x[bad[-1] + 1] if bad[-1] + 1 <= last else None)
+    if x0 is None or x0 > ref[0]:
+        return None, q_ref
+    return float(x0), float(q_ref)
+
+
+def run_paper_case(re_tau, lbu, n_modes=100, seed=1, precision="fp32", stats_every=10, through=10.0,
+                   start=2.0, ref=(12.0, 18.0), tol=0.05):
+    """The channel of Sec. 4.1 at H = lbu cells; returns a dict of results.
+
+    x is measured in delta from the inlet; the reference window for the
+    developed state stays clear of the outlet (zero-gradient, no sponge)."""
+    import torch
+    from .channel import LBMChannel
+    ny = int(lbu)
+    delta = ny / 2.0
+    nx, nz = int(round(20 * delta)), int(round(1.6 * delta))
+    nz += nz % 2
+    ch = LBMChannel(nx, ny, nz, re_tau=re_tau, n_modes=n_modes, seed=seed, precision=precision,
+                    stats_every=stats_every)
+    c = ch.constants()
+    u_b = 0.05
+    T = nx / u_b                                     # domain-through time in steps
+    n0, n1 = int(round(start * T)), int(round(through * T))
+    ch.step(n0)
+    ch.reset_stats()
+    ch.step(n1 - n0)
+    ch.sync()
+    s, ut, n = ch.stats()
+    torch.cuda.synchronize()
+    p = profiles(s, ut, n, nz)
+    x = (np.arange(nx) + 0.5) / delta
+    u_ref = c["utau_ref"]
+    utau = p["utau"].mean(axis=0) / u_ref
+    peak = shear_stress_peak(p["uv"], u_ref)
+    L_ut, ut_dev = adaptation_length(utau, x, ref, tol)
+    L_uv, uv_dev = adaptation_length(peak, x, ref, 2 * tol)
+    res = dict(re_tau=re_tau, lbu=lbu, lattice=[nx, ny, nz], steps=n1, samples=int(n),
+               precision=precision, n_modes=n_modes,
+               utau_developed=ut_dev, uv_peak_developed=uv_dev,
+               adaptation_utau_delta=L_ut, adaptation_uv_delta=L_uv,
+               utau_at_x=dict(zip([1, 2, 4, 6, 8, 10, 12, 16], [
+                   float(utau[min(nx - 1, int(v * delta))]) for v in (1, 2, 4, 6, 8, 10, 12, 16)])),
+               uv_peak_at_x=dict(zip([1, 2, 4, 6, 8, 10, 12, 16], [
+                   float(peak[min(nx - 1, int(v * delta))]) for v in (1, 2, 4, 6, 8, 10, 12, 16)])))
+    ch.close()
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--re-tau", type=float, default=1000.0)
+    ap.add_argument("--lbu", type=int, default=40, help="cells across the channel height H")
+    ap.add_argument("--modes", type=int, default=100)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--through", type=float, default=10.0, help="domain-through times in all")
+    ap.add_argument("--start", type=float, default=2.0, help="domain-through times before statistics")
+    a = ap.parse_args()
+    print(json.dumps(run_paper_case(a.re_tau, a.lbu, n_modes=a.modes, precision=a.precision,
+                                    through=a.through, start=a.start)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
