@@ -5,12 +5,15 @@ Each window starts from the channel's current state, advances it by
 `window` steps, and returns J (by default the Reynolds-stress mismatch J_R at
 a downstream station) with dJ/dtheta from the hand-written adjoint
 (`STGAdjoint`); a torch optimizer then updates theta = (ell_e, amp, kappa, B)
--- only the entries named in `params`, the others keep their values.  The
-inlet's length scale and amplitude act on the flow downstream within the
-acoustic light cone of a window, so the station must lie close enough to the
-inlet (the wave front moves about 0.58 cells per step).
+-- only the entries named in `params`, the others keep their values.  A
+change of the inlet turbulence reaches a downstream station by convection
+(about U_b = 0.05 cells per step), so a window must span that time -- 800
+steps to x = 40 -- or its gradient sees only the acoustic response there and
+points the wrong way; and since one window's J scatters widely in a turbulent
+flow, each update averages several windows.
 
-    python -m paper_2304_04214_gb300.tuning --iters 40
+    python -m paper_2304_04214_gb300.tuning --iters 12 --station 40 --window 2048 \
+        --ckpt-every 64 --windows-per-update 4
 
 prints one JSON line per update (mean J of its windows, theta).
 """
