@@ -126,6 +126,22 @@ int lbm_step(lbm_handle *h, int n);
  * read). */
 int lbm_sync(lbm_handle *h);
 
+/* Checkpoint / resume (the paper has none; this is for long statistics runs).
+ * lbm_save writes the channel's state to the file at path: a header (grid,
+ * storage, creation options, a hash of the STG draws, time, parameters,
+ * statistics sample counters), then the stored populations as raw FP32 or
+ * 16-bit words, u_tau, the FP64 statistics accumulators and, if one was set,
+ * the inlet profile, with a 64-bit FNV-1a checksum over that payload.  It
+ * synchronizes the stream.  lbm_load restores a handle created with the same
+ * grid, storage, Re_tau, options and STG draws: the next steps are
+ * bit-identical to those of the run that saved.  It reads and checks the
+ * whole file before it changes the handle.  Errors: LBM_ESTATE before
+ * lbm_bind_memory; LBM_EINVAL for a file that cannot be opened, read or
+ * written, a foreign or corrupted file (magic, version, sizes, checksum), or
+ * one saved by a channel created differently; LBM_ECUDA. */
+int lbm_save(lbm_handle *h, const char *path);
+int lbm_load(lbm_handle *h, const char *path);
+
 /* Set the CUDA stream later calls enqueue on (cudaStream_t; NULL = default). */
 int lbm_set_stream(lbm_handle *h, void *cuda_stream);
 

@@ -56,6 +56,8 @@ PROTOTYPES = {
     "lbm_step": (ct.c_int, [_h, ct.c_int]),
     "lbm_sync": (ct.c_int, [_h]),
     "lbm_set_stream": (ct.c_int, [_h, ct.c_void_p]),
+    "lbm_save": (ct.c_int, [_h, ct.c_char_p]),
+    "lbm_load": (ct.c_int, [_h, ct.c_char_p]),
     "lbm_set_step_kernel": (ct.c_int, [_h, ct.c_int]),
     "lbm_get_step_kernel": (ct.c_int, [_h, ct.POINTER(ct.c_int)]),
     "lbm_stats": (ct.c_int, [_h, _dp, _dp, ct.POINTER(ct.c_long)]),

@@ -115,6 +115,15 @@ class LBMChannel:
         th = np.ascontiguousarray(theta, dtype=np.float64)
         _abi.check(self.lib.lbm_set_params(self.h, _dptr(th)), "lbm_set_params")
 
+    # ---- checkpoint files ----
+    def save(self, path):
+        """Write the channel's state to `path` (see lbm_save)."""
+        _abi.check(self.lib.lbm_save(self.h, str(path).encode()), "lbm_save")
+
+    def load(self, path):
+        """Restore a state written by save() from a channel created alike."""
+        _abi.check(self.lib.lbm_load(self.h, str(path).encode()), "lbm_load")
+
     # ---- host copies ----
     def fields(self):
         rho = np.empty((self.nz, self.ny, self.nx))

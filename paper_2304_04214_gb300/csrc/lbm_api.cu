@@ -1458,6 +1458,180 @@ int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, 
     return LBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint files: a fixed header, then the payload -- the stored lattice
+// (raw FP32 or 16-bit words), u_tau, the statistics accumulators and, if one
+// was set, the inlet profile -- with a 64-bit FNV-1a checksum over the payload
+// folded eight bytes at a time.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+constexpr char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
+constexpr uint32_t kFileVersion = 1;
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t nx, ny, nz, precision, n_modes, inlet, wall_model, stats_every, custom_profile, pad;
+    int64_t t, n_samples, steps_since_stats;
+    double re_tau, u_bulk, c_smag, kappa0, B0, theta[4];
+    uint64_t uniforms_hash, payload_bytes, checksum;
+};
+
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        size_t i = 0;
+        for (; i + 8 <= n; i += 8) {
+            uint64_t w;
+            std::memcpy(&w, b + i, 8);
+            h = (h ^ w) * 1099511628211ull;
+        }
+        for (; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+};
+
+uint64_t hash_doubles(const std::vector<double> &v) {
+    Fnv f;
+    f.add(v.data(), v.size() * sizeof(double));
+    return f.h;
+}
+
+struct Payload {            // device ranges of the payload, in file order
+    std::vector<std::pair<void *, size_t>> dev;
+};
+
+Payload payload_of(lbm_handle *h) {
+    Payload p;
+    p.dev.push_back({h->lat[h->cur], 19 * (size_t)h->ncell * h->elem});
+    p.dev.push_back({h->d_utau, 2 * (size_t)h->nz * h->nx * sizeof(float)});
+    p.dev.push_back({h->d_st, 7 * (size_t)h->nx * h->ny * sizeof(double)});
+    p.dev.push_back({h->d_st_utau, 2 * (size_t)h->nx * sizeof(double)});
+    return p;
+}
+
+constexpr size_t kChunk = 64u << 20;   // host staging of device ranges
+
+}  // namespace
+
+extern "C" {
+
+int lbm_save(lbm_handle *h, const char *path) {
+    if (!h || !path) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
+    FileHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, kMagic, 8);
+    hd.version = kFileVersion; hd.header_bytes = sizeof(FileHeader);
+    hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.precision = h->opts.precision;
+    hd.n_modes = h->n_modes; hd.inlet = h->opts.inlet; hd.wall_model = h->opts.wall_model;
+    hd.stats_every = h->opts.stats_every; hd.custom_profile = h->custom_profile ? 1 : 0;
+    hd.t = h->t; hd.n_samples = h->n_samples; hd.steps_since_stats = h->steps_since_stats;
+    hd.re_tau = h->re_tau; hd.u_bulk = h->opts.u_bulk; hd.c_smag = h->opts.c_smag;
+    hd.kappa0 = h->opts_kappa0; hd.B0 = h->opts.B;
+    for (int c = 0; c < 4; ++c) hd.theta[c] = h->theta[c];
+    hd.uniforms_hash = hash_doubles(h->uniforms);
+    const Payload pl = payload_of(h);
+    size_t total = 0;
+    for (auto &r : pl.dev) total += r.second;
+    if (h->custom_profile) total += (h->prof_U.size() + h->prof_R.size()) * sizeof(double);
+    hd.payload_bytes = total;
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return LBM_EINVAL;
+    int rc = LBM_OK;
+    Fnv f;
+    std::vector<char> buf(kChunk);
+    if (std::fwrite(&hd, sizeof hd, 1, fp) != 1) rc = LBM_EINVAL;   // checksum patched below
+    for (auto &r : pl.dev) {
+        for (size_t off = 0; rc == LBM_OK && off < r.second; off += kChunk) {
+            const size_t n = std::min(kChunk, r.second - off);
+            if ((e = cudaMemcpy(buf.data(), (char *)r.first + off, n, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+                rc = cuda_fail(e);
+                break;
+            }
+            f.add(buf.data(), n);
+            if (std::fwrite(buf.data(), 1, n, fp) != n) rc = LBM_EINVAL;
+        }
+    }
+    if (rc == LBM_OK && h->custom_profile) {
+        for (const std::vector<double> *v : {&h->prof_U, &h->prof_R}) {
+            f.add(v->data(), v->size() * sizeof(double));
+            if (std::fwrite(v->data(), sizeof(double), v->size(), fp) != v->size()) rc = LBM_EINVAL;
+        }
+    }
+    if (rc == LBM_OK) {
+        hd.checksum = f.h;
+        if (std::fseek(fp, 0, SEEK_SET) != 0 || std::fwrite(&hd, sizeof hd, 1, fp) != 1) rc = LBM_EINVAL;
+    }
+    if (std::fclose(fp) != 0 && rc == LBM_OK) rc = LBM_EINVAL;
+    return rc;
+}
+
+int lbm_load(lbm_handle *h, const char *path) {
+    if (!h || !path) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return LBM_EINVAL;
+    FileHeader hd;
+    int rc = LBM_OK;
+    if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, kMagic, 8) != 0 ||
+        hd.version != kFileVersion || hd.header_bytes != sizeof(FileHeader))
+        rc = LBM_EINVAL;
+    // the file must come from a channel created like this one
+    if (rc == LBM_OK &&
+        (hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.precision != h->opts.precision ||
+         hd.n_modes != h->n_modes || hd.inlet != h->opts.inlet || hd.wall_model != h->opts.wall_model ||
+         hd.stats_every != h->opts.stats_every || hd.re_tau != h->re_tau || hd.u_bulk != h->opts.u_bulk ||
+         hd.c_smag != h->opts.c_smag || hd.kappa0 != h->opts_kappa0 || hd.B0 != h->opts.B ||
+         hd.uniforms_hash != hash_doubles(h->uniforms)))
+        rc = LBM_EINVAL;
+    // read and check the whole payload before touching the handle
+    const Payload pl = payload_of(h);
+    size_t dev_bytes = 0;
+    for (auto &r : pl.dev) dev_bytes += r.second;
+    const size_t prof_n = hd.custom_profile ? 7 * (size_t)h->ny : 0;
+    if (rc == LBM_OK && hd.payload_bytes != dev_bytes + prof_n * sizeof(double)) rc = LBM_EINVAL;
+    std::vector<char> data;
+    std::vector<double> prof(prof_n);
+    if (rc == LBM_OK) {
+        data.resize(dev_bytes);
+        Fnv f;
+        for (size_t off = 0; off < dev_bytes; off += kChunk) {
+            const size_t n = std::min(kChunk, dev_bytes - off);
+            if (std::fread(data.data() + off, 1, n, fp) != n) { rc = LBM_EINVAL; break; }
+            f.add(data.data() + off, n);
+        }
+        if (rc == LBM_OK && prof_n) {
+            if (std::fread(prof.data(), sizeof(double), prof_n, fp) != prof_n) rc = LBM_EINVAL;
+            else f.add(prof.data(), prof_n * sizeof(double));
+        }
+        if (rc == LBM_OK && (f.h != hd.checksum || std::fgetc(fp) != EOF)) rc = LBM_EINVAL;
+    }
+    std::fclose(fp);
+    if (rc) return rc;
+    // parameters and inlet profile (host tables, uploaded), then the device state
+    h->custom_profile = false;
+    if ((rc = lbm_set_params(h, hd.theta)) != LBM_OK) return rc;
+    if (prof_n && (rc = lbm_set_inlet_profile(h, prof.data(), prof.data() + h->ny)) != LBM_OK) return rc;
+    cudaError_t e;
+    size_t off = 0;
+    for (auto &r : pl.dev) {
+        if ((e = cudaMemcpy(r.first, data.data() + off, r.second, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e);
+        off += r.second;
+    }
+    h->t = hd.t;
+    h->n_samples = (long)hd.n_samples;
+    h->steps_since_stats = hd.steps_since_stats;
+    h->stg_len = 0;                              // the STG ring is refilled at the next step
+    return cuda_fail(cudaStreamSynchronize(h->stream));
+}
+
 void lbm_destroy(lbm_handle *h) {
     if (!h) return;
     if (h->adj.owns && h->adj.mem) { cudaStreamSynchronize(h->stream); cudaFree(h->adj.mem); }

@@ -108,3 +108,14 @@ def test_step_kernel_selection_is_checked_on_the_host():
     assert lib.lbm_set_step_kernel(h, _abi.LBM_KERNEL_PAIR) == 0
     assert lib.lbm_get_step_kernel(h, ct.byref(k)) == 0 and k.value == _abi.LBM_KERNEL_PAIR
     lib.lbm_destroy(h)
+
+
+def test_checkpoint_calls_refuse_before_binding():
+    lib = _abi.lib()
+    rc, h = _create()
+    assert rc == 0
+    assert lib.lbm_save(h, b"/nonexistent/x.lbm") == _abi.LBM_ESTATE
+    assert lib.lbm_load(h, b"/nonexistent/x.lbm") == _abi.LBM_ESTATE
+    assert lib.lbm_save(h, None) == _abi.LBM_EINVAL
+    assert lib.lbm_save(None, b"x") == _abi.LBM_EINVAL
+    lib.lbm_destroy(h)
