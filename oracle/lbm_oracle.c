@@ -35,6 +35,9 @@
  *   A14    f^neq = w/(2 cs^4) Q:Pi;  A15 unknown f^neq from the opposite
  *   A16    STG spectrum / modes / length scale (see stg_tables)
  *   A18    zero-gradient outlet copy;  A19 order of the boundary passes
+ *   A24    outlet sponge (Sec. 4.1 names one; its form is not given): over
+ *          the last L cells the viscosity rises by nu_s r^2, r = (x - (nx -
+ *          L)) / L at the cell centre x = i + 1/2, so tau0(x) = tau0 + 3 nu_s r^2
  */
 #include <stdlib.h>
 #include <string.h>
@@ -125,6 +128,8 @@ typedef struct {
     double beta_kmin;/* k_min = beta 2 pi / max l_e */
     double tau0;     /* > 0 overrides tau0 = 3 nu + 1/2 */
     double body_force[3];   /* uniform force density (tests only) */
+    int sponge_cells;       /* outlet sponge thickness in cells (0: none), reading A24 */
+    double sponge_nu;       /* viscosity added at the outlet end of the sponge */
 } orc_config;
 
 typedef struct orc {
@@ -685,7 +690,14 @@ static void one_step(orc *h) {
                     h->F[3 * c + a] += h->c.body_force[a];
                     Fc[a] = h->F[3 * c + a];
                 }
-                collide_cell(pc, Fc, tau0, cs, mrt, out, &r, u);
+                double t0c = tau0;
+                if (h->c.sponge_cells > 0) {           /* A24 */
+                    const double L = h->c.sponge_cells;
+                    double ramp = (i + 0.5 - (nx - L)) / L;
+                    ramp = ramp < 0.0 ? 0.0 : (ramp > 1.0 ? 1.0 : ramp);
+                    t0c = tau0 + 3.0 * h->c.sponge_nu * ramp * ramp;
+                }
+                collide_cell(pc, Fc, t0c, cs, mrt, out, &r, u);
                 for (int q = 0; q < Q; ++q) h->f[(long)q * n + c] = out[q];
                 h->rho[c] = r;
                 for (int a = 0; a < 3; ++a) h->u[3 * c + a] = u[a];

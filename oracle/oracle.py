@@ -28,6 +28,7 @@ class OracleConfig(ct.Structure):
         ("kappa0", ct.c_double), ("B0", ct.c_double),
         ("k_ratio", ct.c_double), ("beta_kmin", ct.c_double),
         ("tau0", ct.c_double), ("body_force", ct.c_double * 3),
+        ("sponge_cells", ct.c_int), ("sponge_nu", ct.c_double),
     ]
 
 

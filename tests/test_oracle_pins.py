@@ -472,3 +472,39 @@ def test_complex_step_gradient_matches_central_differences():
         fd = (jp - jm) / (2 * d)
         scale = max(abs(cs), 1e-8)
         assert abs(cs - fd) < 1e-6 * scale + 1e-12, (kk, cs, fd)
+
+
+def test_outlet_sponge_raises_the_local_viscosity_by_its_ramp():
+    """Reading A24: over the last L cells the viscosity rises by nu_s r^2.
+    A shear wave u_y = U sin(k z) in a periodic box decays, column by column,
+    at the local rate (nu + nu_s r(x)^2) k^2 -- checked between steps 5 and
+    20 (after the start-up from equilibrium) within 3%, inside and outside
+    the sponge, except the three columns on each side of the periodic wrap,
+    where the sponge's most viscous end meets its start and viscous diffusion
+    along x mixes their rates."""
+    from oracle.oracle import Oracle, cell_api, default_config
+    nx, ny, nz, L, nu_s, tau0 = 32, 4, 32, 16, 0.1, 0.8
+    cfg = default_config(nx, ny, nz, n_modes=0, inlet=0, walls=2, wall_model=0, c_smag=0.0, tau0=tau0,
+                         sponge_cells=L, sponge_nu=nu_s)
+    o = Oracle(cfg, theta=(0.4, 1.0, 0.4, 7.8), uniforms=None)
+    _, w, c = cell_api.matrix()
+    k = 2 * np.pi / nz
+    z = np.arange(nz) + 0.5
+    uy = 1e-3 * np.sin(k * z)                         # (nz,)
+    cu = c[:, 1][:, None] * uy[None, :]               # (Q, nz)
+    feq = w[:, None] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * uy[None, :] ** 2)
+    f0 = np.broadcast_to(feq[:, :, None, None], (19, nz, ny, nx)).copy()
+    o.set_state(f0)
+    amp = []
+    for n in (5, 15):
+        o.step(n)
+        _, u = o.fields()
+        amp.append(np.abs((u[..., 1] * np.sin(k * z)[:, None, None]).sum(axis=(0, 1))))   # per x
+    rate = -np.log(amp[1] / amp[0]) / 15
+    xc = np.arange(nx) + 0.5
+    ramp = np.clip((xc - (nx - L)) / L, 0, 1)
+    expect = ((tau0 - 0.5) / 3 + nu_s * ramp ** 2) * k * k
+    err = (rate / expect - 1)[3:nx - 3]
+    assert np.max(np.abs(err)) < 0.03, np.round(err, 4)
+    # the rate inside the sponge differs from outside by what the ramp adds
+    assert rate[nx - 4] / rate[nx // 4] > 1.5
