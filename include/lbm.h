@@ -167,6 +167,17 @@ int lbm_set_step_kernel(lbm_handle *h, int kind);
 /* The kernel later steps will run (AUTO resolved) into *kind. */
 int lbm_get_step_kernel(const lbm_handle *h, int *kind);
 
+/* Outlet sponge zone (Sec. 4.1 places one before the outlet; its form is not
+ * given, reading A24): over the last `cells` cells the kinematic viscosity
+ * rises by nu_max r^2, r in [0, 1] the position of the cell centre in the
+ * zone, so tau0 of those cells is tau0 + 3 nu_max r^2 (the Smagorinsky part
+ * is added on top as everywhere).  Damps what the outlet would reflect.
+ * cells = 0 or nu_max = 0: none (the default).  Applies to later steps and
+ * to the forward and adjoint steps of lbm_adjoint_step; saved in checkpoint
+ * files.  Errors: LBM_EINVAL for cells outside [0, nx] or nu_max negative or
+ * not finite. */
+int lbm_set_sponge(lbm_handle *h, int cells, double nu_max);
+
 /* Statistics accumulated every stats_every steps since the last reset:
  * sums[(j*nx + i)*7 + c], c = (u, v, w, uu, vv, ww, uv), each summed over z
  * and samples in FP64; utau_sums[w*nx + i] (w = 0 bottom, 1 top) summed over z

@@ -111,6 +111,11 @@ class LBMChannel:
     def step_kernel(self, name):
         _abi.check(self.lib.lbm_set_step_kernel(self.h, _abi.KERNELS[name]), "lbm_set_step_kernel")
 
+    def set_sponge(self, cells, nu_max):
+        """Outlet sponge: over the last `cells` cells the viscosity rises by
+        nu_max r^2 (r the position in the zone); cells = 0 switches it off."""
+        _abi.check(self.lib.lbm_set_sponge(self.h, int(cells), float(nu_max)), "lbm_set_sponge")
+
     def set_params(self, theta):
         th = np.ascontiguousarray(theta, dtype=np.float64)
         _abi.check(self.lib.lbm_set_params(self.h, _dptr(th)), "lbm_set_params")

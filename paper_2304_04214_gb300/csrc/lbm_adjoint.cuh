@@ -244,6 +244,7 @@ struct AdjArgs {
     int nx, ny, nz;
     int inlet, wall_model;
     float tau0, csm18, y1_nu, kappa, B;
+    float sp_x0, sp_inv, sp_3nu;    // outlet sponge as in StepArgs
 };
 
 // Pull source of population q (compile-time after unrolling) from the
@@ -376,8 +377,9 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
         luy = cj * (uu - a.jr_mean[j]);
     }
     AdjIn A;
-    if (is_wall) collide_adjoint<true>(lam, P, f9, Fx, 0.f, Fz, a.tau0, a.csm18, lux, luy, 0.f, A);
-    else collide_adjoint<false>(lam, P, f9, 0.f, 0.f, 0.f, a.tau0, a.csm18, lux, luy, 0.f, A);
+    const float t0c = sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, G.ic);
+    if (is_wall) collide_adjoint<true>(lam, P, f9, Fx, 0.f, Fz, t0c, a.csm18, lux, luy, 0.f, A);
+    else collide_adjoint<false>(lam, P, f9, 0.f, 0.f, 0.f, t0c, a.csm18, lux, luy, 0.f, A);
 
     // ---- reverse of the wall model (implicit function theorem for u_tau) ----
     if (WALLBLOCK && a.wall_model) {

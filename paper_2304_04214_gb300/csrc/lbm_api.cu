@@ -125,6 +125,8 @@ struct lbm_handle {
     long long stg_t0 = 0, stg_len = 0;
     long long check_every = 16;
     int step_kind = LBM_KERNEL_AUTO;    // step kernel variant (lbm_set_step_kernel)
+    int sponge_cells = 0;               // outlet sponge (lbm_set_sponge): thickness, added viscosity
+    double sponge_nu = 0.0;
     // tensor maps of the lattices the staged kernel has read (base -> map)
     struct MapEntry { const void *base = nullptr; CUtensorMap map; };
     MapEntry maps[32];
@@ -578,6 +580,14 @@ cudaError_t launch_staged(lbm_handle *h, const lbmk::StepArgs<S> &a, const void 
     return cudaGetLastError();
 }
 
+// The outlet sponge as kernel arguments: zone start, 1 / length, 3 nu_s.
+void sponge_args(const lbm_handle *h, float &x0, float &inv, float &s3nu) {
+    const int L = h->sponge_cells;
+    x0 = (float)(h->nx - L);
+    inv = L > 0 ? 1.0f / (float)L : 0.0f;
+    s3nu = L > 0 ? (float)(3.0 * h->sponge_nu) : 0.0f;
+}
+
 template <class S>
 cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
     using T = typename S::T;
@@ -604,6 +614,7 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
     a.y1_nu = (float)(0.5 / h->nu);
     a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
     a.obj = io.obj; a.obj_i0 = io.obj_i0; a.obj_i1 = io.obj_i1; a.obj_iR = io.obj_iR;
+    sponge_args(h, a.sp_x0, a.sp_inv, a.sp_3nu);
     const int bxmax = lbmk::STEP_THREADS / lbmk::BY;
     const size_t slot = h->prof_on ? prof_slot(h) : 0;
     if (h->prof_on) cudaEventRecord(h->ev0[slot], h->stream);
@@ -734,6 +745,7 @@ void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lou
     a.csm18 = (float)(18.0 * std::sqrt(2.0) * h->opts.c_smag);
     a.y1_nu = (float)(0.5 / h->nu);
     a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
+    sponge_args(h, a.sp_x0, a.sp_inv, a.sp_3nu);
     // wall rows and their second rows on the side stream, the rest on the
     // handle's stream (disjoint writes), joined before anything that follows
     const int bx = 64;
@@ -935,6 +947,13 @@ int lbm_set_step_kernel(lbm_handle *h, int kind) {
 int lbm_get_step_kernel(const lbm_handle *h, int *kind) {
     if (!h || !kind) return LBM_EINVAL;
     *kind = resolve_kind(h);
+    return LBM_OK;
+}
+
+int lbm_set_sponge(lbm_handle *h, int cells, double nu_max) {
+    if (!h || cells < 0 || cells > h->nx || !(nu_max >= 0.0) || !std::isfinite(nu_max)) return LBM_EINVAL;
+    h->sponge_cells = nu_max > 0.0 ? cells : 0;
+    h->sponge_nu = cells > 0 ? nu_max : 0.0;
     return LBM_OK;
 }
 
@@ -1469,14 +1488,14 @@ int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, 
 namespace {
 
 constexpr char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
-constexpr uint32_t kFileVersion = 1;
+constexpr uint32_t kFileVersion = 2;
 
 struct FileHeader {
     char magic[8];
     uint32_t version, header_bytes;
-    int32_t nx, ny, nz, precision, n_modes, inlet, wall_model, stats_every, custom_profile, pad;
+    int32_t nx, ny, nz, precision, n_modes, inlet, wall_model, stats_every, custom_profile, sponge_cells;
     int64_t t, n_samples, steps_since_stats;
-    double re_tau, u_bulk, c_smag, kappa0, B0, theta[4];
+    double re_tau, u_bulk, c_smag, kappa0, B0, theta[4], sponge_nu;
     uint64_t uniforms_hash, payload_bytes, checksum;
 };
 
@@ -1531,6 +1550,7 @@ int lbm_save(lbm_handle *h, const char *path) {
     hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.precision = h->opts.precision;
     hd.n_modes = h->n_modes; hd.inlet = h->opts.inlet; hd.wall_model = h->opts.wall_model;
     hd.stats_every = h->opts.stats_every; hd.custom_profile = h->custom_profile ? 1 : 0;
+    hd.sponge_cells = h->sponge_cells; hd.sponge_nu = h->sponge_nu;
     hd.t = h->t; hd.n_samples = h->n_samples; hd.steps_since_stats = h->steps_since_stats;
     hd.re_tau = h->re_tau; hd.u_bulk = h->opts.u_bulk; hd.c_smag = h->opts.c_smag;
     hd.kappa0 = h->opts_kappa0; hd.B0 = h->opts.B;
@@ -1596,6 +1616,7 @@ int lbm_load(lbm_handle *h, const char *path) {
     for (auto &r : pl.dev) dev_bytes += r.second;
     const size_t prof_n = hd.custom_profile ? 7 * (size_t)h->ny : 0;
     if (rc == LBM_OK && hd.payload_bytes != dev_bytes + prof_n * sizeof(double)) rc = LBM_EINVAL;
+    if (rc == LBM_OK && (hd.sponge_cells < 0 || hd.sponge_cells > h->nx || !(hd.sponge_nu >= 0.0))) rc = LBM_EINVAL;
     std::vector<char> data;
     std::vector<double> prof(prof_n);
     if (rc == LBM_OK) {
@@ -1625,6 +1646,8 @@ int lbm_load(lbm_handle *h, const char *path) {
             return cuda_fail(e);
         off += r.second;
     }
+    h->sponge_cells = hd.sponge_cells;
+    h->sponge_nu = hd.sponge_nu;
     h->t = hd.t;
     h->n_samples = (long)hd.n_samples;
     h->steps_since_stats = hd.steps_since_stats;

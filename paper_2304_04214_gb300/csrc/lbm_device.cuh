@@ -372,7 +372,7 @@ __device__ __forceinline__ void make_pairs2(const V2 (&f)[19], Pairs2 &P) {
 // wall force (Fx, 0, Fz) per cell -- the wall-model force is tangential, so
 // its y component is zero by construction (eq:force_wm, the wall normal is y).
 template <bool SHIFTED, bool HAS_FORCE>
-__device__ __forceinline__ void collide_pairs2(const Pairs2 &P, V2 (&f)[19], V2 Fx, V2 Fz, float tau0,
+__device__ __forceinline__ void collide_pairs2(const Pairs2 &P, V2 (&f)[19], V2 Fx, V2 Fz, V2 tau0,
                                                float csm18, V2 &ux_o, V2 &uy_o, V2 &uz_o) {
     const V2 *s = P.s, *d = P.d;
     const V2 f9 = P.f9, s04 = P.s04, s13 = P.s13, s57 = P.s57, s26 = P.s26;
@@ -418,7 +418,7 @@ __device__ __forceinline__ void collide_pairs2(const Pairs2 &P, V2 (&f)[19], V2 
     const V2 pzz = vfma(-0.5f, n11, pyz_common);
     V2 qq = vfma(pxx, pxx, vfma(pyy, pyy, pzz * pzz));
     qq = vfma(2.0f * n13, n13, vfma(2.0f * n14, n14, vfma(2.0f * n15, n15, qq)));
-    const V2 tt = vdup(tau0);
+    const V2 tt = tau0;
     const V2 sv = 2.0f * vrcp(tt + vsqrt(vfma(csm18 * vsqrt(qq), irho, tt * tt)));
     // relaxation: G_k = s_k n_k / |row_k|^2
     V2 G1 = n1 * (S_E / 2394.0f), G2 = n2 * (S_EPS / 252.0f);
@@ -479,7 +479,7 @@ __device__ __forceinline__ void collide_pairs2(const Pairs2 &P, V2 (&f)[19], V2 
 
 // Force-free collision of two cells (interior rows).
 template <bool SHIFTED>
-__device__ __forceinline__ void collide_mrt2(V2 (&f)[19], float tau0, float csm18, V2 &ux_o, V2 &uy_o,
+__device__ __forceinline__ void collide_mrt2(V2 (&f)[19], V2 tau0, float csm18, V2 &ux_o, V2 &uy_o,
                                              V2 &uz_o) {
     Pairs2 P;
     make_pairs2<SHIFTED>(f, P);
@@ -529,12 +529,30 @@ struct StepArgs {
     int check;                               // test |u| < 0.3 and finiteness this step
     int reverse;                             // traverse the lattice backwards this step
     float tau0, csm18;                       // tau0, 18 sqrt2 C_smag
+    float sp_x0, sp_inv, sp_3nu;             // outlet sponge: start x, 1 / length, 3 nu_s (0: none)
     float y1_nu, kappa, B;                   // y1 / nu, Reichardt constants
     // objective accumulators (null: none): [0] sum of tau_w over the wall cells
     // with obj_i0 <= i < obj_i1; [1 + 3j ..] sums over z of u, v, u v at i = obj_iR
     double *obj;
     int obj_i0, obj_i1, obj_iR;
 };
+
+// tau0 of a cell at x = i + 1/2 with the outlet sponge (reading A24): the
+// viscosity rises by nu_s r^2 over the zone, r the position in it.
+__device__ __forceinline__ float sponge_tau0(float tau0, float x0, float inv, float s3nu, int i) {
+    if (s3nu == 0.0f) return tau0;
+    const float r = fminf(fmaxf(((float)i + 0.5f - x0) * inv, 0.0f), 1.0f);
+    return fmaf(s3nu, r * r, tau0);
+}
+template <class S>
+__device__ __forceinline__ float cell_tau0(const StepArgs<S> &a, int i) {
+    return sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, i);
+}
+template <class S>
+__device__ __forceinline__ V2 pair_tau0(const StepArgs<S> &a, int i0) {
+    return make_float2(cell_tau0(a, i0), cell_tau0(a, i0 + 1));
+}
+
 
 constexpr int BY = 2;  // rows per block: (0,1) and (ny-2,ny-1) share a block
 constexpr int WALL_THREADS = 128;   // threads (x-cells) per block of the wall-row kernel
@@ -697,8 +715,8 @@ __device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k
             fwp[0] = Fx; fwp[1] = Fy; fwp[2] = Fz;
         }
     }
-    if (a.wall_model && is_wall) collide_mrt<S::SHIFTED, true>(f, P, Fx, Fy, Fz, a.tau0, a.csm18, ux, uy, uz);
-    else collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, a.tau0, a.csm18, ux, uy, uz);
+    if (a.wall_model && is_wall) collide_mrt<S::SHIFTED, true>(f, P, Fx, Fy, Fz, cell_tau0(a, i), a.csm18, ux, uy, uz);
+    else collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, cell_tau0(a, i), a.csm18, ux, uy, uz);
     if (valid) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
 }
 
@@ -736,7 +754,7 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, LBM_STEP_MINB) step_kernel(c
     Pairs P;
     make_pairs<S::SHIFTED>(f, P);
     float ux, uy, uz;
-    collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, a.tau0, a.csm18, ux, uy, uz);
+    collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, cell_tau0(a, i), a.csm18, ux, uy, uz);
     if (i < nx) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
 }
 
@@ -877,8 +895,9 @@ __global__ void __launch_bounds__(WALL_THREADS) wall_kernel(const __grid_constan
         Fz = make_float2(Fo[0][1], Fo[1][1]);
     }
     V2 ux, uy, uz;
-    if (a.wall_model) collide_pairs2<S::SHIFTED, true>(P, f, Fx, Fz, a.tau0, a.csm18, ux, uy, uz);
-    else collide_pairs2<S::SHIFTED, false>(P, f, Fx, Fz, a.tau0, a.csm18, ux, uy, uz);
+    const V2 t0w = vdup(cell_tau0(a, ic));           // bottom and top cells share x
+    if (a.wall_model) collide_pairs2<S::SHIFTED, true>(P, f, Fx, Fz, t0w, a.csm18, ux, uy, uz);
+    else collide_pairs2<S::SHIFTED, false>(P, f, Fx, Fz, t0w, a.csm18, ux, uy, uz);
     if (a.obj) {                                     // objective sums (launch-uniform branch)
         float tw = 0.0f;
         if (valid && i >= a.obj_i0 && i < a.obj_i1)
@@ -958,7 +977,7 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, Step2Blocks<S>::value) step2
         for (int q = 0; q < 19; ++q) f[q].x = fl[q];
     }
     V2 ux, uy, uz;
-    collide_mrt2<S::SHIFTED>(f, a.tau0, a.csm18, ux, uy, uz);
+    collide_mrt2<S::SHIFTED>(f, pair_tau0(a, i0), a.csm18, ux, uy, uz);
     if (!valid) return;
     if (a.obj && (i0 == a.obj_iR || i0 + 1 == a.obj_iR)) {     // J_R sums at x = i_R
         const float u = i0 == a.obj_iR ? ux.x : ux.y, v = i0 == a.obj_iR ? uy.x : uy.y;
@@ -1041,8 +1060,8 @@ __global__ void __launch_bounds__(64, 2 * LBM_STEP4_MINB) step4_kernel(const __g
         for (int q = 0; q < 19; ++q) fa[q].x = fl[q];
     }
     V2 uxa, uya, uza, uxb, uyb, uzb;
-    collide_mrt2<S::SHIFTED>(fa, a.tau0, a.csm18, uxa, uya, uza);
-    collide_mrt2<S::SHIFTED>(fb, a.tau0, a.csm18, uxb, uyb, uzb);
+    collide_mrt2<S::SHIFTED>(fa, pair_tau0(a, x0), a.csm18, uxa, uya, uza);
+    collide_mrt2<S::SHIFTED>(fb, pair_tau0(a, x0 + 2), a.csm18, uxb, uyb, uzb);
     if (!valid) return;
     const int c = o00 + x0;
 #pragma unroll

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(SG_THREADS, StagedCfg<S>::MINB)
             for (int q = 0; q < 19; ++q) f[q].x = fl[q];
         }
         V2 ux, uy, uz;
-        collide_mrt2<S::SHIFTED>(f, a.tau0, a.csm18, ux, uy, uz);
+        collide_mrt2<S::SHIFTED>(f, pair_tau0(a, i0), a.csm18, ux, uy, uz);
         if (!valid) continue;
         const int c = (k * ny + j) * nx + i0;
 #pragma unroll

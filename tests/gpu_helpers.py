@@ -9,7 +9,7 @@ Q = 19
 
 
 def make_pair(nx, ny, nz, re_tau=1000.0, n_modes=16, seed=1, precision="fp32", inlet=1,
-              wall_model=1, c_smag=0.01, theta=(0.4, 1.0, 0.4, 7.8), stats=0):
+              wall_model=1, c_smag=0.01, theta=(0.4, 1.0, 0.4, 7.8), stats=0, sponge=(0, 0.0)):
     """Oracle and CUDA channel on the same inputs.  The library fixes u_tau,ref
     and nu from the (kappa, B) it is created with, so the oracle's creation
     constants kappa0, B0 are theta's."""
@@ -17,12 +17,14 @@ def make_pair(nx, ny, nz, re_tau=1000.0, n_modes=16, seed=1, precision="fp32", i
     un = stg_uniforms(n_modes, seed) if n_modes > 0 else None
     cfg = default_config(nx, ny, nz, re_tau=re_tau, n_modes=n_modes, inlet=inlet,
                          wall_model=wall_model, c_smag=c_smag, stats=stats,
-                         kappa0=theta[2], B0=theta[3])
+                         kappa0=theta[2], B0=theta[3], sponge_cells=sponge[0], sponge_nu=sponge[1])
     o = Oracle(cfg, theta=theta, uniforms=un)
     g = LBMChannel(nx, ny, nz, re_tau=re_tau, n_modes=n_modes, uniforms=un, precision=precision,
                    inlet=bool(inlet), wall_model=bool(wall_model), c_smag=c_smag,
                    ell_e=theta[0], amp=theta[1], kappa=theta[2], B=theta[3],
                    stats_every=1 if stats else 0)
+    if sponge[0] > 0:
+        g.set_sponge(*sponge)
     return o, g
 
 

@@ -173,3 +173,29 @@ def test_adjoint_full_window_256x64x64(kk):
     assert abs(J - Jo) <= 1e-4 * abs(Jo), (J, Jo)
     ref = Jim / H
     assert abs(dJ[kk] - ref) <= 1e-3 * abs(ref), (kk, dJ[kk], ref)
+
+
+def test_vjp_with_the_outlet_sponge_matches_complex_step():
+    """lbm_vjp_step with the sponge over the last 8 of 24 cells: state and
+    theta products against the oracle's complex-step derivative."""
+    nx, ny, nz, N, seed, theta = 24, 8, 4, 8, 21, (0.4, 1.0, 0.4, 7.8)
+    o, g = make_pair(nx, ny, nz, n_modes=N, seed=seed, theta=theta, sponge=(8, 0.05))
+    f0 = set_both(o, g, o.state() * (1.0 + 0.01 * noise((19, nz, ny, nx), seed=seed + 1)))
+    lam = noise((19, nz, ny, nx), seed=31)
+    prev, dth = _vjp(g, lam)
+    v = noise((19, nz, ny, nx), seed=32)
+    cfg = default_config(nx, ny, nz, n_modes=N, kappa0=theta[2], B0=theta[3], sponge_cells=8, sponge_nu=0.05)
+    oz = Oracle(cfg, theta=theta, uniforms=stg_uniforms(N, seed), complex_step=True)
+    oz.set_state(f0, H * v)
+    oz.step(1)
+    ref = np.sum(lam * oz.state(imag=True)) / H
+    got = np.sum(prev * v)
+    assert abs(got - ref) <= 1e-3 * abs(ref), (got, ref)
+    for kk in (0, 2):
+        im = np.zeros(4)
+        im[kk] = H
+        oz = Oracle(cfg, theta=theta, uniforms=stg_uniforms(N, seed), complex_step=True, theta_im=im)
+        oz.set_state(f0)
+        oz.step(1)
+        ref = np.sum(lam * oz.state(imag=True)) / H
+        assert abs(dth[kk] - ref) <= 1e-3 * abs(ref) + 1e-9, (kk, dth[kk], ref)

@@ -38,6 +38,7 @@ def _custom_profile(ch):
 def test_resume_is_bit_identical(tmp_path, precision):
     a = _channel(precision)
     _custom_profile(a)
+    a.set_sponge(12, 0.05)            # restored from the file too
     a.step(7)
     path = tmp_path / "a.lbm"
     a.save(path)
