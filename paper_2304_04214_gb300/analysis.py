@@ -60,11 +60,13 @@ def adaptation_length(q, x, ref, tol):
 
 
 def run_paper_case(re_tau, lbu, n_modes=100, seed=1, precision="fp32", stats_every=10, through=10.0,
-                   start=2.0, ref=(12.0, 18.0), tol=0.05):
+                   start=2.0, ref=(12.0, 18.0), tol=0.05, sponge_delta=0.0, sponge_nu=0.1):
     """The channel of Sec. 4.1 at H = lbu cells; returns a dict of results.
 
     x is measured in delta from the inlet; the reference window for the
-    developed state stays clear of the outlet (zero-gradient, no sponge)."""
+    developed state stays clear of the outlet.  sponge_delta > 0 adds the
+    outlet sponge of that thickness (in delta) with viscosity sponge_nu at
+    its end (Sec. 4.1 uses 1 delta; the form is reading A24)."""
     import torch
     from .channel import LBMChannel
     ny = int(lbu)
@@ -73,6 +75,8 @@ def run_paper_case(re_tau, lbu, n_modes=100, seed=1, precision="fp32", stats_eve
     nz += nz % 2
     ch = LBMChannel(nx, ny, nz, re_tau=re_tau, n_modes=n_modes, seed=seed, precision=precision,
                     stats_every=stats_every)
+    if sponge_delta > 0:
+        ch.set_sponge(int(round(sponge_delta * delta)), sponge_nu)
     c = ch.constants()
     u_b = 0.05
     T = nx / u_b                                     # domain-through time in steps
@@ -91,7 +95,8 @@ def run_paper_case(re_tau, lbu, n_modes=100, seed=1, precision="fp32", stats_eve
     L_ut, ut_dev = adaptation_length(utau, x, ref, tol)
     L_uv, uv_dev = adaptation_length(peak, x, ref, 2 * tol)
     res = dict(re_tau=re_tau, lbu=lbu, lattice=[nx, ny, nz], steps=n1, samples=int(n),
-               precision=precision, n_modes=n_modes,
+               precision=precision, n_modes=n_modes, sponge_delta=sponge_delta,
+               sponge_nu=sponge_nu if sponge_delta > 0 else 0.0,
                utau_developed=ut_dev, uv_peak_developed=uv_dev,
                adaptation_utau_delta=L_ut, adaptation_uv_delta=L_uv,
                utau_at_x=dict(zip([1, 2, 4, 6, 8, 10, 12, 16], [
@@ -110,9 +115,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--through", type=float, default=10.0, help="domain-through times in all")
     ap.add_argument("--start", type=float, default=2.0, help="domain-through times before statistics")
+    ap.add_argument("--sponge", type=float, default=0.0, help="outlet sponge thickness in delta (0: none)")
+    ap.add_argument("--sponge-nu", type=float, default=0.1, help="viscosity added at the sponge's end")
     a = ap.parse_args()
     print(json.dumps(run_paper_case(a.re_tau, a.lbu, n_modes=a.modes, precision=a.precision,
-                                    through=a.through, start=a.start)), flush=True)
+                                    through=a.through, start=a.start, sponge_delta=a.sponge,
+                                    sponge_nu=a.sponge_nu)), flush=True)
 
 
 if __name__ == "__main__":
