@@ -799,7 +799,7 @@ __device__ __forceinline__ void inlet_velocity(const StepArgs<S> &a, int j, int 
 // regularized inlet at x = 0; the wall model (Sec. 2.3, Algorithm 1 steps
 // 9-14) with a scalar Newton solve; then the packed collision with the force.
 template <class S, bool STATS>
-__global__ void __launch_bounds__(WALL_THREADS) wall_kernel(const __grid_constant__ StepArgs<S> a) {
+__global__ void __launch_bounds__(WALL_THREADS, 4) wall_kernel(const __grid_constant__ StepArgs<S> a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
