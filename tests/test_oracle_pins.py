@@ -411,6 +411,37 @@ def test_mass_and_momentum_conservation_periodic():
                        j0 + 4 * 8 * 6 * 5 * np.array([1e-5, -2e-5, 3e-5]), atol=1e-13)
 
 
+def test_streaming_moves_the_mass_centroid_by_the_momentum():
+    """Streaming carries each post-collision population f*_q from x to x + c_q,
+    and the collision keeps every cell's mass and momentum when F = 0, so one
+    step moves the first moment of mass, sum_x x rho(x), by exactly the total
+    momentum sum_x sum_q c_q f_q.  Checked on a localized disturbance of the
+    rest state in a periodic box (away from the wrap), along all three axes:
+    a pull from the wrong side, or a velocity read with a wrong sign,
+    reverses or scrambles the shift."""
+    nx, ny, nz = 12, 10, 8
+    cfg = default_config(nx, ny, nz, n_modes=0, inlet=0, walls=2, wall_model=0, c_smag=0.01)
+    o = Oracle(cfg)
+    _, w, c = cell_api.matrix()
+    f0 = np.broadcast_to(w[:, None, None, None], (Q, nz, ny, nx)).copy()
+    blob = (slice(None), slice(2, 6), slice(3, 7), slice(4, 8))
+    f0[blob] *= 1.0 + 0.2 * noise((Q, 4, 4, 4), seed=11)
+    o.set_state(f0)
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pos = (ii, jj, kk)
+
+    def centroid(f):
+        rho = f.sum(axis=0)
+        return np.array([(p * rho).sum() for p in pos])
+
+    j0 = np.einsum("qkji,qa->a", f0, c)
+    assert np.min(np.abs(j0)) > 1e-3                   # a shift along every axis
+    x0 = centroid(f0)
+    o.step(1)
+    x1 = centroid(o.state())
+    assert np.allclose(x1 - x0, j0, rtol=0, atol=1e-11), (x1 - x0, j0)
+
+
 def test_slip_walls_conserve_mass_and_tangential_momentum():
     cfg = default_config(8, 6, 5, n_modes=0, inlet=0, walls=0, wall_model=0, c_smag=0.01)
     o = Oracle(cfg)
