@@ -442,6 +442,29 @@ def test_streaming_moves_the_mass_centroid_by_the_momentum():
     assert np.allclose(x1 - x0, j0, rtol=0, atol=1e-11), (x1 - x0, j0)
 
 
+def test_outlet_is_transparent_to_a_streamwise_uniform_flow():
+    """Reading A18: the zero-gradient outlet continues the field past x = nx-1
+    as if it did not change along x.  So a state uniform in x (any y, z
+    dependence) must evolve in the inlet/outlet channel exactly as in a
+    periodic one wherever the inlet's disturbance has not arrived: after n
+    steps on every column i > n, the outlet column included.  Checked with
+    the slip walls, the wall model and the SGS closure on."""
+    nx, ny, nz, n = 16, 8, 6, 5
+    _, w, c = cell_api.matrix()
+    base = w[:, None, None] * (1.0 + 0.05 * noise((Q, nz, ny), seed=12))
+    f0 = np.broadcast_to(base[..., None], (Q, nz, ny, nx)).copy()
+    runs = []
+    for inlet in (1, 0):
+        cfg = default_config(nx, ny, nz, n_modes=8, inlet=inlet, walls=0, wall_model=1, c_smag=0.01)
+        o = Oracle(cfg, theta=(0.4, 1.0, 0.4, 7.8), uniforms=stg_uniforms(8, 2))
+        o.set_state(f0)
+        o.step(n)
+        runs.append(o.state())
+    a, b = runs
+    assert np.max(np.abs(a[..., n + 1:] - b[..., n + 1:])) < 1e-15
+    assert np.max(np.abs(a[..., 0] - b[..., 0])) > 1e-6      # the inlet did act
+
+
 def test_slip_walls_conserve_mass_and_tangential_momentum():
     cfg = default_config(8, 6, 5, n_modes=0, inlet=0, walls=0, wall_model=0, c_smag=0.01)
     o = Oracle(cfg)
