@@ -499,6 +499,45 @@ def test_wall_force_opposes_the_flow_with_reichardt_stress():
     assert np.allclose(-F[:, 0, :, 0], rho[:, 0, :] * ut[0] ** 2, rtol=1e-13)
 
 
+def test_wall_force_follows_the_tangential_velocity_of_the_second_cell():
+    """Sec. 2.3 with readings A9-A11 on a disturbed state (rho != 1 and a
+    wall-normal velocity at the second cell): the force on a first-layer cell
+    is -rho_w u_tau^2 e_x, e_x the unit vector of the second cell's velocity
+    with its wall-normal part removed, u_tau solving the wall law for the
+    first-layer velocity projected on e_x, the force's sign following that
+    projection (reading A10).  The bottom first layer starts mirrored in x, so
+    there it flows against the second cell and the projection turns negative.
+    Everything is rebuilt from the fields the step collided with
+    (rho u0 = rho u - F/2)."""
+    nx, ny, nz = 8, 12, 6
+    _, _, c = cell_api.matrix()
+    o = Oracle(default_config(nx, ny, nz, n_modes=0))
+    f0 = o.state() * (1.0 + 0.03 * noise((Q, nz, ny, nx), seed=13))
+    mirror = [int(np.nonzero((c == c[q] * np.array([-1, 1, 1])).all(axis=1))[0][0]) for q in range(Q)]
+    f0[:, :, 0, :] = f0[mirror, :, 0, :]
+    o.set_state(f0)
+    o.step(1)
+    F = o.force()
+    rho, u = o.fields()
+    nu = o.constants()["nu"]
+    ut = o.utau()
+    for w, (jw, j2) in enumerate(((0, 1), (ny - 1, ny - 2))):
+        u2 = u[:, j2, :, :].copy()
+        assert np.max(np.abs(u2[..., 1])) > 1e-4         # a wall-normal part to remove
+        u2[..., 1] = 0.0
+        ex = u2 / np.linalg.norm(u2, axis=-1, keepdims=True)
+        rw = rho[:, jw, :]
+        assert np.max(np.abs(rw - 1.0)) > 1e-3
+        u0 = u[:, jw, :, :] - 0.5 * F[:, jw, :, :] / rw[..., None]
+        uhat = np.einsum("kia,kia->ki", u0, ex)
+        assert (uhat < 0).mean() > 0.5 if w == 0 else (uhat > 0).all()
+        t = ut[w]
+        law = t * np.vectorize(cell_api.reichardt)(0.5 * t / nu)
+        assert np.max(np.abs(law - np.abs(uhat))) < 1e-14
+        expect = -(rw * t * t * np.sign(uhat))[..., None] * ex
+        assert np.max(np.abs(F[:, jw, :, :] - expect)) < 1e-15
+
+
 # --------------------------------------------------------------------------
 # Complex-step derivatives agree with central differences
 # --------------------------------------------------------------------------
