@@ -538,6 +538,56 @@ def test_wall_force_follows_the_tangential_velocity_of_the_second_cell():
         assert np.max(np.abs(F[:, jw, :, :] - expect)) < 1e-15
 
 
+def test_statistics_and_objective_are_window_means_of_the_collided_fields():
+    """The FP64 statistics are z-sums of (u, v, w, uu, vv, ww, uv) per (y, x)
+    and of u_tau per (wall, x), one sample per step; the adjoint objective is
+    J = J_tau + J_R with J_tau the mean of tau_w / u_tau,ref^2 = rho_w u_tau^2 /
+    u_tau,ref^2 over the window and the wall cells i0 <= i < i1 of both walls,
+    and J_R = sum_j (<u'v'>(iR, j) / u_tau,ref^2 - R12+(j))^2 with the
+    prescribed R12+ of reading A16 (vi), negative in the lower half.  All of
+    it is rebuilt here from the per-step fields, with R12+ from its closed
+    form."""
+    nx, ny, nz, N, T = 16, 12, 6, 12, 5
+    i0, i1, iR = 3, 9, 7
+    re_tau = 1000.0
+    o = Oracle(default_config(nx, ny, nz, n_modes=N, re_tau=re_tau, stats=1),
+               theta=(0.4, 1.0, 0.4, 7.8), uniforms=stg_uniforms(N, 3))
+    o.step(3)
+    o.stats_reset()
+    o.objective_begin(i0, i1, iR)
+    ur2 = o.constants()["utau_ref"] ** 2
+    sums = np.zeros((ny, nx, 7))
+    ut_sums = np.zeros((2, nx))
+    jt, su, sv, suv = 0.0, np.zeros(ny), np.zeros(ny), np.zeros(ny)
+    for _ in range(T):
+        o.step(1)
+        rho, u = o.fields()
+        ut = o.utau()
+        uu, vv, ww = u[..., 0], u[..., 1], u[..., 2]
+        for a, q in enumerate((uu, vv, ww, uu * uu, vv * vv, ww * ww, uu * vv)):
+            sums[..., a] += q.sum(axis=0)
+        ut_sums += ut.sum(axis=1)
+        jt += (rho[:, 0, i0:i1] * ut[0][:, i0:i1] ** 2).sum() + (rho[:, -1, i0:i1] * ut[1][:, i0:i1] ** 2).sum()
+        su += uu[:, :, iR].sum(axis=0)
+        sv += vv[:, :, iR].sum(axis=0)
+        suv += (uu * vv)[:, :, iR].sum(axis=0)
+    s, uts, n = o.stats()
+    assert n == T
+    assert np.allclose(s, sums, rtol=1e-14, atol=1e-17)
+    assert np.allclose(uts, ut_sums, rtol=1e-14, atol=1e-17)
+    delta = ny / 2
+    y = np.arange(ny) + 0.5
+    d = np.minimum(y, ny - y)
+    sh = (1 - d / delta) * (1 - np.exp(-d * re_tau / delta / 26.0)) ** 2
+    r12 = np.where(y < delta, -sh, sh)
+    cnt = T * nz
+    J_tau = jt / (T * 2 * (i1 - i0) * nz) / ur2
+    J_R = (((suv / cnt - su / cnt * sv / cnt) / ur2 - r12) ** 2).sum()
+    _, _, parts = o.objective()
+    assert abs(parts[0] - J_tau) < 1e-12 * J_tau
+    assert abs(parts[1] - J_R) < 1e-12 * J_R
+
+
 # --------------------------------------------------------------------------
 # Complex-step derivatives agree with central differences
 # --------------------------------------------------------------------------
