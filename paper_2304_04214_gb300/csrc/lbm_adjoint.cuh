@@ -264,7 +264,7 @@ __device__ __forceinline__ int src_off(int q, const PullGeom &g) {
     return g.o00 + oy + oz + x;
 }
 
-template <bool WALLBLOCK>
+template <bool WALLBLOCK, bool SPONGE>
 __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int k, int tx, float (*sh)[4]) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const bool valid = i < nx;
@@ -377,7 +377,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
         luy = cj * (uu - a.jr_mean[j]);
     }
     AdjIn A;
-    const float t0c = sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, G.ic);
+    const float t0c = SPONGE ? sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, G.ic) : a.tau0;
     if (is_wall) collide_adjoint<true>(lam, P, f9, Fx, 0.f, Fz, t0c, a.csm18, lux, luy, 0.f, A);
     else collide_adjoint<false>(lam, P, f9, 0.f, 0.f, 0.f, t0c, a.csm18, lux, luy, 0.f, A);
 
@@ -527,19 +527,25 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
 // memory.  Launched beside the interior kernel: every pushed entry has one
 // writer (the outlet entries take atomics), so the two never write the same
 // word.
+template <bool SPONGE>
 __global__ void __launch_bounds__(128, 4) adjoint_wall_kernel(const __grid_constant__ AdjArgs a) {
     __shared__ float sh[128 / BY][4];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y == 0 ? threadIdx.y : a.ny - 2 + threadIdx.y;
-    adjoint_cell<true>(a, i, j, blockIdx.z, threadIdx.x, sh);
+    adjoint_cell<true, SPONGE>(a, i, j, blockIdx.z, threadIdx.x, sh);
 }
 
 // Rows 2 .. ny-3.  Latency-bound: five resident blocks per SM (a register
-// budget of 102) beat four without spills.
-__global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__ AdjArgs a) {
+// budget of 102) beat four without spills.  SPONGE: the outlet sponge is on
+// (a separate instantiation keeps the per-cell tau0 out of the plain kernel).
+#ifndef LBM_ADJ_MINB
+#define LBM_ADJ_MINB 5
+#endif
+template <bool SPONGE>
+__global__ void __launch_bounds__(128, LBM_ADJ_MINB) adjoint_kernel(const __grid_constant__ AdjArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = 2 + blockIdx.y * BY + threadIdx.y;
-    adjoint_cell<false>(a, i, j, blockIdx.z, threadIdx.x, nullptr);
+    adjoint_cell<false, SPONGE>(a, i, j, blockIdx.z, threadIdx.x, nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -753,9 +753,15 @@ void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lou
     const int nbx = (h->nx + bx - 1) / bx;
     cudaEventRecord(h->ev_fork, h->stream);
     cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-    lbmk::adjoint_wall_kernel<<<dim3(nbx, 2, h->nz), block, 0, h->side>>>(a);
+    const bool sponge = a.sp_3nu != 0.0f;
+    const dim3 gw(nbx, 2, h->nz), gi(nbx, (h->ny - 4) / lbmk::BY, h->nz);
+    if (sponge) lbmk::adjoint_wall_kernel<true><<<gw, block, 0, h->side>>>(a);
+    else lbmk::adjoint_wall_kernel<false><<<gw, block, 0, h->side>>>(a);
     cudaEventRecord(h->ev_join, h->side);
-    if (h->ny > 4) lbmk::adjoint_kernel<<<dim3(nbx, (h->ny - 4) / lbmk::BY, h->nz), block, 0, h->stream>>>(a);
+    if (h->ny > 4) {
+        if (sponge) lbmk::adjoint_kernel<true><<<gi, block, 0, h->stream>>>(a);
+        else lbmk::adjoint_kernel<false><<<gi, block, 0, h->stream>>>(a);
+    }
     cudaStreamWaitEvent(h->stream, h->ev_join, 0);
     h->launches += 2;
 }
