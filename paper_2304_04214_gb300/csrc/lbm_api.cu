@@ -630,7 +630,13 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
         if ((err = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess ||
             (err = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess)
             return err;
-        const dim3 wgrid((h->nx + lbmk::WALL_THREADS - 1) / lbmk::WALL_THREADS, h->nz);
+        // a wall plane takes ~10 us beside the interior kernel: walk up to
+        // four planes per block while that stays well inside the interior
+        // kernel's time (its bytes at ~6.5 TB/s)
+        const double interior_us = (double)h->nx * h->ny * h->nz * (sizeof(typename S::T) * 38.0) / 6.5e6;
+        a.wall_planes = std::max(1, std::min(4, (int)(interior_us / 12.0)));
+        const dim3 wgrid((h->nx + lbmk::WALL_THREADS - 1) / lbmk::WALL_THREADS,
+                         (h->nz + a.wall_planes - 1) / a.wall_planes);
         if (io.stats) lbmk::wall_kernel<S, true><<<wgrid, lbmk::WALL_THREADS, 0, h->side>>>(a);
         else lbmk::wall_kernel<S, false><<<wgrid, lbmk::WALL_THREADS, 0, h->side>>>(a);
         if ((err = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return err;

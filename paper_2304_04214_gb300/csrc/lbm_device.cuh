@@ -528,6 +528,7 @@ struct StepArgs {
     int inlet, wall_model;
     int check;                               // test |u| < 0.3 and finiteness this step
     int reverse;                             // traverse the lattice backwards this step
+    int wall_planes;                         // z planes each wall-kernel block walks
     float tau0, csm18;                       // tau0, 18 sqrt2 C_smag
     float sp_x0, sp_inv, sp_3nu;             // outlet sponge: start x, 1 / length, 3 nu_s (0: none)
     float y1_nu, kappa, B;                   // y1 / nu, Reichardt constants
@@ -798,11 +799,18 @@ __device__ __forceinline__ void inlet_velocity(const StepArgs<S> &a, int j, int 
 // the second cell (row 1 / ny - 2) summed from its pulled populations; the
 // regularized inlet at x = 0; the wall model (Sec. 2.3, Algorithm 1 steps
 // 9-14) with a scalar Newton solve; then the packed collision with the force.
+// Each block walks a.wall_planes consecutive z planes: the kernel is a long
+// dependent chain per cell with few warps, so fewer, longer-lived blocks hold
+// fewer of the registers the interior kernel beside it could use, as long as
+// the walk still ends inside the interior kernel's time.
 template <class S, bool STATS>
 __global__ void __launch_bounds__(WALL_THREADS, 4) wall_kernel(const __grid_constant__ StepArgs<S> a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y;
+#pragma unroll 1
+    for (int kk = 0; kk < a.wall_planes; ++kk) {
+    const int k = blockIdx.y * a.wall_planes + kk;
+    if (k >= nz) return;
     const bool valid = i < nx;
     const int ic = valid ? i : nx - 1;
     int xm = ic - 1, xp = ic + 1;                    // sources for c_x = +1 / -1
@@ -914,7 +922,7 @@ __global__ void __launch_bounds__(WALL_THREADS, 4) wall_kernel(const __grid_cons
             atomicAdd(a.obj + 3 + 3 * (ny - 1), (double)(ux.y * uy.y));
         }
     }
-    if (!valid) return;
+    if (!valid) continue;
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         S::st(a.out[q] + ob + i, f[q].x);
@@ -928,6 +936,7 @@ __global__ void __launch_bounds__(WALL_THREADS, 4) wall_kernel(const __grid_cons
     if (a.check) {
         const V2 uu = vfma(ux, ux, vfma(uy, uy, uz * uz));
         if (!(uu.x < 0.09f) || !(uu.y < 0.09f)) atomicAdd(a.flags + 1, 1u);   // also catches NaN
+    }
     }
 }
 
