@@ -675,6 +675,20 @@ cudaError_t launch_step_io(lbm_handle *h, const StepIO &io) {
     }
 }
 
+// STG field of steps a.t0 .. a.t0 + a.nsteps - 1: four time levels per thread
+// when there are enough of them to fill the blocks, else one
+void launch_stg_kernel(lbm_handle *h, const lbmk::StgArgs &a, cudaStream_t st) {
+    const int n = a.nsteps, nbz = (h->nz + lbmk::STG_KZ - 1) / lbmk::STG_KZ;
+    if (n >= 4 * lbmk::STG_KT) {
+        const dim3 grid(nbz, h->ny, (n + 4 * lbmk::STG_KT - 1) / (4 * lbmk::STG_KT));
+        lbmk::stg_kernel<4><<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, st>>>(a);
+    } else {
+        const dim3 grid(nbz, h->ny, (n + lbmk::STG_KT - 1) / lbmk::STG_KT);
+        lbmk::stg_kernel<1><<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, st>>>(a);
+    }
+    h->launches += 1;
+}
+
 // STG inlet velocities of steps t0 .. t0 + n - 1 into the ring slots 0 .. n-1.
 void launch_stg(lbm_handle *h, long long t0, int n, bool apply_profile) {
     lbmk::StgArgs a;
@@ -682,9 +696,7 @@ void launch_stg(lbm_handle *h, long long t0, int n, bool apply_profile) {
     a.sqsig = h->d_sqsig; a.amat = h->d_amat; a.UR = h->d_UR; a.out = h->d_uin;
     a.t0 = t0; a.nsteps = n; a.apply_profile = apply_profile ? 1 : 0;
     a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
-    dim3 grid((h->nz + lbmk::STG_KZ - 1) / lbmk::STG_KZ, h->ny, (n + lbmk::STG_KT - 1) / lbmk::STG_KT);
-    lbmk::stg_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, h->stream>>>(a);
-    h->launches += 1;
+    launch_stg_kernel(h, a, h->stream);
 }
 
 int one_step(lbm_handle *h) {
@@ -710,7 +722,7 @@ int one_step(lbm_handle *h) {
         h->n_samples += 1;
         const int cols = (h->nx * h->ny + lbmk::ST_COLS - 1) / lbmk::ST_COLS;
         const int tb = lbmk::ST_COLS * lbmk::ST_CHUNKS;
-        const int blocks = cols + (h->opts.wall_model ? (2 * h->nx + tb - 1) / tb : 0);
+        const int blocks = cols + (h->opts.wall_model ? (2 * h->nx + lbmk::ST_COLS - 1) / lbmk::ST_COLS : 0);
         lbmk::stats_kernel<<<blocks, tb, 0, h->stream>>>(
             h->d_ubuf, h->d_utau, h->d_st, h->d_st_utau, h->nx, h->ny, h->nz, h->ncell, h->opts.wall_model);
         h->launches += 1;
@@ -727,9 +739,7 @@ void launch_stg_into(lbm_handle *h, float *out, long long t0, int n, cudaStream_
     a.sqsig = h->d_sqsig; a.amat = h->d_amat; a.UR = h->d_UR; a.out = out;
     a.t0 = t0; a.nsteps = n; a.apply_profile = 0;
     a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
-    dim3 grid((h->nz + lbmk::STG_KZ - 1) / lbmk::STG_KZ, h->ny, (n + lbmk::STG_KT - 1) / lbmk::STG_KT);
-    lbmk::stg_kernel<<<grid, lbmk::STG_KZ * lbmk::STG_KT, 0, st>>>(a);
-    h->launches += 1;
+    launch_stg_kernel(h, a, st);
 }
 
 // One adjoint step: s_n (FP32 lattice) and lambda_{n+1} -> lambda_n.

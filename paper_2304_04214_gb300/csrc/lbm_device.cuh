@@ -1115,48 +1115,71 @@ struct StgArgs {
 
 constexpr int STG_KZ = 32, STG_KT = 8, STG_MCHUNK = 256;
 
+// Block = STG_KZ planes k x STG_KT thread rows, each row TT consecutive time
+// levels, for one row j; the modes are taken in chunks whose phases (per time
+// level) and amplitude/direction entries are staged in shared memory.  A
+// thread loads the mode's beta_n(k) once for its TT levels.
+template <int TT>
 __global__ void __launch_bounds__(STG_KZ * STG_KT) stg_kernel(const __grid_constant__ StgArgs a) {
-    __shared__ uint32_t s_ph[STG_KT][STG_MCHUNK];   // alpha + phi + time part, per time level
+    constexpr int NT = STG_KT * TT;                  // time levels per block
+    __shared__ __align__(16) uint32_t s_ph[STG_MCHUNK][NT];   // alpha + phi + time part
     __shared__ float4 s_sq[STG_MCHUNK];
     const int j = blockIdx.y;
-    const int lz = threadIdx.x % STG_KZ, lt = threadIdx.x / STG_KZ;
+    const int lz = threadIdx.x % STG_KZ, lt0 = (threadIdx.x / STG_KZ) * TT;
     const int k = blockIdx.x * STG_KZ + lz;
-    const int ts = blockIdx.z * STG_KT + lt;
     const int N = a.n_modes;
-    float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+    float vx[TT], vy[TT], vz[TT];
+#pragma unroll
+    for (int tt = 0; tt < TT; ++tt) vx[tt] = vy[tt] = vz[tt] = 0.0f;
     for (int n0 = 0; n0 < N; n0 += STG_MCHUNK) {
         const int nc = min(STG_MCHUNK, N - n0);
         __syncthreads();
-        for (int e = threadIdx.x; e < STG_KT * nc; e += blockDim.x) {
-            const int tl = e / nc, n = n0 + e % nc;
-            const uint64_t t = (uint64_t)(a.t0 + (long long)blockIdx.z * STG_KT + tl);
-            s_ph[tl][e % nc] = a.alpha[(size_t)j * N + n] + a.phi32[n] + (uint32_t)((a.rate64[n] * t) >> 32);
+        for (int e = threadIdx.x; e < NT * nc; e += blockDim.x) {
+            const int m = e / NT, tl = e % NT, n = n0 + m;
+            const uint64_t t = (uint64_t)(a.t0 + (long long)blockIdx.z * NT + tl);
+            s_ph[m][tl] = a.alpha[(size_t)j * N + n] + a.phi32[n] + (uint32_t)((a.rate64[n] * t) >> 32);
         }
         for (int e = threadIdx.x; e < nc; e += blockDim.x) s_sq[e] = a.sqsig[(size_t)j * N + n0 + e];
         __syncthreads();
         if (k < a.nz) {
             const uint32_t *be = a.betaT + (size_t)n0 * a.nz + k;
-#pragma unroll 4
+#pragma unroll 2
             for (int m = 0; m < nc; ++m) {
-                const uint32_t ph = s_ph[lt][m] + be[(size_t)m * a.nz];
-                const float x = (float)(int32_t)ph * 1.4629180792671596e-09f;   // 2 pi / 2^32
+                const uint32_t b = be[(size_t)m * a.nz];
                 const float4 qs = s_sq[m];
-                const float cw = qs.x * __cosf(x);
-                vx = fmaf(cw, qs.y, vx);
-                vy = fmaf(cw, qs.z, vy);
-                vz = fmaf(cw, qs.w, vz);
+                uint32_t ph[TT];
+                if constexpr (TT == 4) {
+                    const uint4 p4 = *reinterpret_cast<const uint4 *>(&s_ph[m][lt0]);
+                    ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+                } else {
+#pragma unroll
+                    for (int tt = 0; tt < TT; ++tt) ph[tt] = s_ph[m][lt0 + tt];
+                }
+#pragma unroll
+                for (int tt = 0; tt < TT; ++tt) {
+                    const float x = (float)(int32_t)(ph[tt] + b) * 1.4629180792671596e-09f;   // 2 pi / 2^32
+                    const float cw = qs.x * __cosf(x);
+                    vx[tt] = fmaf(cw, qs.y, vx[tt]);
+                    vy[tt] = fmaf(cw, qs.z, vy[tt]);
+                    vz[tt] = fmaf(cw, qs.w, vz[tt]);
+                }
             }
         }
     }
-    if (k >= a.nz || ts >= a.nsteps) return;
-    float *o = a.out + (((size_t)ts * a.nz + k) * a.ny + j) * 3;
-    if (a.apply_profile) {
-        const float *m = a.amat + 6 * j;
-        o[0] = a.UR[j] + m[0] * vx;
-        o[1] = m[1] * vx + m[2] * vy;
-        o[2] = m[3] * vx + m[4] * vy + m[5] * vz;
-    } else {
-        o[0] = vx; o[1] = vy; o[2] = vz;
+    if (k >= a.nz) return;
+#pragma unroll
+    for (int tt = 0; tt < TT; ++tt) {
+        const int ts = blockIdx.z * NT + lt0 + tt;
+        if (ts >= a.nsteps) break;
+        float *o = a.out + (((size_t)ts * a.nz + k) * a.ny + j) * 3;
+        if (a.apply_profile) {
+            const float *m = a.amat + 6 * j;
+            o[0] = a.UR[j] + m[0] * vx[tt];
+            o[1] = m[1] * vx[tt] + m[2] * vy[tt];
+            o[2] = m[3] * vx[tt] + m[4] * vy[tt] + m[5] * vz[tt];
+        } else {
+            o[0] = vx[tt]; o[1] = vy[tt]; o[2] = vz[tt];
+        }
     }
 }
 
@@ -1202,7 +1225,8 @@ __global__ void fields_kernel(const typename S::T *f, const float *fw, float *rh
 // z-sums of the velocity moments added to the FP64 accumulators.  Block =
 // 32 consecutive (i, j) columns x 8 chunks of z; each thread sums its chunk in
 // FP32, the chunks are combined in shared memory and one thread per column adds
-// the sample to the FP64 sums.  Blocks past the columns do the u_tau sums.
+// the sample to the FP64 sums.  The blocks past the columns do the u_tau sums
+// the same way, over 32 consecutive (wall, i) entries each.
 constexpr int ST_COLS = 32, ST_CHUNKS = 8;
 __global__ void __launch_bounds__(ST_COLS * ST_CHUNKS) stats_kernel(
         const float *__restrict__ ubuf, const float *__restrict__ utau, double *st, double *st_utau, int nx,
@@ -1237,12 +1261,20 @@ __global__ void __launch_bounds__(ST_COLS * ST_CHUNKS) stats_kernel(
             }
         }
     } else if (wall) {
-        const int r = ((int)blockIdx.x - nblk_cols) * blockDim.x + threadIdx.x;
+        const int r = ((int)blockIdx.x - nblk_cols) * ST_COLS + col;   // entry w * nx + i
+        float s = 0.0f;
         if (r < 2 * nx) {
             const int w = r / nx, i = r % nx;
-            float s = 0;
-            for (int k = 0; k < nz; ++k) s += utau[((size_t)w * nz + k) * nx + i];
-            st_utau[w * nx + i] += (double)s;
+#pragma unroll 4
+            for (int k = ch; k < nz; k += ST_CHUNKS) s += utau[((size_t)w * nz + k) * nx + i];
+        }
+        part[ch][0][col] = s;
+        __syncthreads();
+        if (ch == 0 && r < 2 * nx) {
+            float a = 0.0f;
+#pragma unroll
+            for (int c = 0; c < ST_CHUNKS; ++c) a += part[c][0][col];
+            st_utau[r] += (double)a;
         }
     }
 }
