@@ -120,9 +120,14 @@ struct lbm_handle {
     float *d_UR = nullptr, *d_amat = nullptr;
     float4 *d_sqsig = nullptr;
     uint32_t *d_alpha = nullptr, *d_betaT = nullptr, *d_phi32 = nullptr;
-    // STG ring: inlet velocities of steps [stg_t0, stg_t0 + stg_len)
+    // STG ring, two halves of stg_ring time levels: the half in use holds the
+    // inlet fluctuations of steps [stg_t0, stg_t0 + stg_len); the other one is
+    // refilled on the aux stream, beside those steps, for the steps from
+    // stg_next_t0 on (-1: no refill pending)
     int stg_ring = 1;
-    long long stg_t0 = 0, stg_len = 0;
+    int stg_half = 0;
+    long long stg_t0 = 0, stg_len = 0, stg_next_t0 = -1;
+    cudaEvent_t ev_stg_free = nullptr, ev_stg_ready = nullptr;
     long long check_every = 16;
     int step_kind = LBM_KERNEL_AUTO;    // step kernel variant (lbm_set_step_kernel)
     int sponge_cells = 0;               // outlet sponge (lbm_set_sponge): thickness, added viscosity
@@ -164,9 +169,11 @@ struct lbm_handle {
         lat[1] = ar.take<char>(19 * (size_t)ncell * elem);
         d_utau = ar.take<float>(2 * (size_t)nz * nx);
         d_fw = ar.take<float>(6 * (size_t)nz * nx);
-        // ring of STG inlet velocities: as many time levels as fit in ~16 MB (<= 64)
-        stg_ring = (int)std::max<size_t>(1, std::min<size_t>(64, (16u << 20) / (12 * (size_t)nz * ny)));
-        d_uin = ar.take<float>(3 * (size_t)nz * ny * stg_ring);
+        // STG ring: two halves of 64 time levels each, fewer where a half
+        // would exceed both 8 MB and 1/32 of the two lattices
+        const size_t half_budget = std::max<size_t>(8u << 20, 2 * 19 * elem * (size_t)ncell / 32);
+        stg_ring = (int)std::max<size_t>(1, std::min<size_t>(64, half_budget / (12 * (size_t)nz * ny)));
+        d_uin = ar.take<float>(3 * (size_t)nz * ny * stg_ring * 2);
         d_ubuf = opts.stats_every > 0 ? ar.take<float>(3 * (size_t)ncell) : nullptr;
         d_st = ar.take<double>(7 * (size_t)nx * ny);
         d_st_utau = ar.take<double>(2 * (size_t)nx);
@@ -422,15 +429,26 @@ struct lbm_handle {
         return true;
     }
 
+    // Forget the STG ring (its tables or the time changed); later work on the
+    // handle's stream is ordered after a refill still running on the aux stream.
+    void stg_reset() {
+        if (stg_next_t0 >= 0) cudaStreamWaitEvent(stream, ev_stg_ready, 0);
+        stg_len = 0;
+        stg_next_t0 = -1;
+    }
+
+    // first time level of half b of the STG ring
+    float *stg_slot(int b) const { return d_uin + 3 * (size_t)nz * ny * stg_ring * b; }
+
     cudaError_t upload_tables() {
         const size_t N = n_modes > 0 ? n_modes : 1;
         cudaError_t e;
+        stg_reset();                            // the tables feed the ring
 #define UP(dst, vec) if ((e = cudaMemcpyAsync(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return e
         UP(d_UR, UR); UP(d_amat, amat); UP(d_sqsig, sqsig);
         UP(d_alpha, alpha); UP(d_betaT, betaT); UP(d_phi32, phi32); UP(d_rate64, rate64);
 #undef UP
         (void)N;
-        stg_len = 0;                            // the STG ring is stale
         return cudaStreamSynchronize(stream);   // host vectors may change after return
     }
 };
@@ -689,7 +707,8 @@ void launch_stg_kernel(lbm_handle *h, const lbmk::StgArgs &a, cudaStream_t st) {
     h->launches += 1;
 }
 
-// STG inlet velocities of steps t0 .. t0 + n - 1 into the ring slots 0 .. n-1.
+// STG inlet velocities of steps t0 .. t0 + n - 1 into the first n slots of
+// the ring, on the handle's stream
 void launch_stg(lbm_handle *h, long long t0, int n, bool apply_profile) {
     lbmk::StgArgs a;
     a.alpha = h->d_alpha; a.betaT = h->d_betaT; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
@@ -699,6 +718,8 @@ void launch_stg(lbm_handle *h, long long t0, int n, bool apply_profile) {
     launch_stg_kernel(h, a, h->stream);
 }
 
+void launch_stg_into(lbm_handle *h, float *out, long long t0, int n, cudaStream_t st);
+
 int one_step(lbm_handle *h) {
     bool stats = false;
     if (h->opts.stats_every > 0) {
@@ -706,16 +727,31 @@ int one_step(lbm_handle *h) {
         if (h->steps_since_stats >= h->opts.stats_every) { stats = true; h->steps_since_stats = 0; }
     }
     if (h->opts.inlet && (h->t < h->stg_t0 || h->t >= h->stg_t0 + h->stg_len)) {
+        if (h->stg_next_t0 >= 0 && h->t == h->stg_next_t0) {
+            // the other half was refilled for these steps on the aux stream
+            cudaStreamWaitEvent(h->stream, h->ev_stg_ready, 0);
+            h->stg_half ^= 1;
+        } else {
+            h->stg_reset();
+            launch_stg_into(h, h->stg_slot(h->stg_half), h->t, h->stg_ring, h->stream);
+        }
         h->stg_t0 = h->t;
         h->stg_len = h->stg_ring;
-        launch_stg(h, h->stg_t0, h->stg_ring, false);
+        // refill the other half for the steps after these, beside them; the
+        // refill waits for the steps enqueued so far, which read that half
+        cudaEventRecord(h->ev_stg_free, h->stream);
+        cudaStreamWaitEvent(h->aux, h->ev_stg_free, 0);
+        launch_stg_into(h, h->stg_slot(h->stg_half ^ 1), h->stg_t0 + h->stg_ring, h->stg_ring, h->aux);
+        cudaEventRecord(h->ev_stg_ready, h->aux);
+        h->stg_next_t0 = h->stg_t0 + h->stg_ring;
     }
     StepIO io;
     io.in = h->lat[h->cur];
     io.out = h->lat[h->cur ^ 1];
     io.utau = h->d_utau;
     io.fw = h->d_fw;
-    io.vprime = h->opts.inlet ? h->d_uin + 3 * (size_t)h->nz * h->ny * (size_t)(h->t - h->stg_t0) : h->d_uin;
+    io.vprime = h->opts.inlet ? h->stg_slot(h->stg_half) + 3 * (size_t)h->nz * h->ny * (size_t)(h->t - h->stg_t0)
+                              : h->d_uin;
     io.stats = stats;
     if (cudaError_t le = launch_step_io(h, io)) return cuda_fail(le);
     if (stats) {
@@ -899,7 +935,9 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_aux_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_aux_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_aux_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_stg_free, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_stg_ready, cudaEventDisableTiming) != cudaSuccess) {
         if (h->owns) cudaFree(h->mem);
         h->mem = nullptr;
         return cuda_fail(cudaGetLastError());
@@ -1117,8 +1155,8 @@ int lbm_get_constants(const lbm_handle *h, double out[6]) {
 int lbm_inlet_velocity(lbm_handle *h, long t, double *out) {
     if (!h || !out || t < 0) return LBM_EINVAL;
     if (!h->bound) return LBM_ESTATE;
+    h->stg_reset();                              // the call writes into the ring
     launch_stg(h, t, 1, true);
-    h->stg_len = 0;
     cudaError_t e;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     const size_t n = 3 * (size_t)h->ny * h->nz;
@@ -1673,12 +1711,15 @@ int lbm_load(lbm_handle *h, const char *path) {
     h->t = hd.t;
     h->n_samples = (long)hd.n_samples;
     h->steps_since_stats = hd.steps_since_stats;
-    h->stg_len = 0;                              // the STG ring is refilled at the next step
+    h->stg_reset();                              // the STG ring is refilled at the next step
     return cuda_fail(cudaStreamSynchronize(h->stream));
 }
 
 void lbm_destroy(lbm_handle *h) {
     if (!h) return;
+    // no work of the handle may still run when its memory goes
+    if (h->aux) cudaStreamSynchronize(h->aux);
+    if (h->side) cudaStreamSynchronize(h->side);
     if (h->adj.owns && h->adj.mem) { cudaStreamSynchronize(h->stream); cudaFree(h->adj.mem); }
     if (h->bound) cudaStreamSynchronize(h->stream);
     for (size_t c = 0; c < h->ev0.size(); ++c) { cudaEventDestroy(h->ev0[c]); cudaEventDestroy(h->ev1[c]); }
@@ -1691,6 +1732,8 @@ void lbm_destroy(lbm_handle *h) {
     if (h->aux) { cudaStreamSynchronize(h->aux); cudaStreamDestroy(h->aux); }
     if (h->ev_aux_fork) cudaEventDestroy(h->ev_aux_fork);
     if (h->ev_aux_join) cudaEventDestroy(h->ev_aux_join);
+    if (h->ev_stg_free) cudaEventDestroy(h->ev_stg_free);
+    if (h->ev_stg_ready) cudaEventDestroy(h->ev_stg_ready);
     delete h;
 }
 
