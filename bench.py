@@ -57,6 +57,9 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+PROF_EVERY = 16
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("lbm_device.cuh", "lbm_staged.cuh"):    # the kernel sources
@@ -243,7 +246,10 @@ def run_native(args, cfg, ws, rank, local):
     barrier()
 
     # ---- timed region: K steps, device events, kernel events, clocks ----
-    _abi.check(lib.lbm_profile_enable(h, 1), "lbm_profile_enable")
+    # the step kernels of every PROF_EVERY-th step are bracketed by events on
+    # the library's stream (an event pair costs the stream a few us, so
+    # timing every step would inflate the step it measures)
+    _abi.check(lib.lbm_profile_enable(h, PROF_EVERY), "lbm_profile_enable")
     ms_k, nk, nall = ct.c_double(), ct.c_long(), ct.c_long()
     lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))   # reset counters
     e0 = torch.cuda.Event(enable_timing=True)
@@ -341,6 +347,7 @@ def run_native(args, cfg, ws, rank, local):
                          "frac": round(achieved / peaks["hbm_gbs"], 4),
                          "traffic": traffic, "peak_source": peak_kind,
                          "kernel": KERNEL_NAMES[kernel], "kernel_ms": round(kern_ms, 5),
+                         "timed_launches": nk.value, "timed_every": PROF_EVERY,
                          "algorithmic_bytes": alg_bytes},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e, 1), "unit": "MLUPS",

@@ -262,10 +262,14 @@ int lbm_wall_shear_async(lbm_handle *h, double *out);
 #define LBM_NOALLOC_MAX_NX 32768
 int lbm_wall_shear_noalloc(lbm_handle *h, double *out);
 
-/* Instrumentation.  While enabled, every launch of the fused step kernel is
- * bracketed by CUDA events on the handle's stream.  read synchronizes and
- * returns the summed kernel time in ms and the number of timed launches since
- * the last read, and the number of kernels of any kind the handle launched. */
+/* Instrumentation.  While enabled (on > 0), every on-th launch of the fused
+ * step kernel (interior and wall rows, from the first one after the call) is
+ * bracketed by CUDA events on the handle's stream: on = 1 times every step,
+ * a larger on samples them (each event pair costs the stream a few
+ * microseconds).  on = 0 disables; on < 0 is LBM_EINVAL.  read synchronizes
+ * and returns the summed kernel time in ms and the number of timed launches
+ * since the last read, and the number of kernels of any kind the handle
+ * launched. */
 int lbm_profile_enable(lbm_handle *h, int on);
 int lbm_profile_read(lbm_handle *h, double *ms_total, long *step_launches, long *all_launches);
 

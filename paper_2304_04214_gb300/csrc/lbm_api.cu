@@ -156,6 +156,8 @@ struct lbm_handle {
     cudaEvent_t stage_ev = nullptr;        // last upload from the staging buffer
     // instrumentation
     bool prof_on = false;
+    int prof_every = 1;                    // time every prof_every-th step launch
+    long long prof_count = 0;
     std::vector<cudaEvent_t> ev0, ev1;
     std::vector<char> ev_busy;
     size_t ev_next = 0;
@@ -634,8 +636,9 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
     a.obj = io.obj; a.obj_i0 = io.obj_i0; a.obj_i1 = io.obj_i1; a.obj_iR = io.obj_iR;
     sponge_args(h, a.sp_x0, a.sp_inv, a.sp_3nu);
     const int bxmax = lbmk::STEP_THREADS / lbmk::BY;
-    const size_t slot = h->prof_on ? prof_slot(h) : 0;
-    if (h->prof_on) cudaEventRecord(h->ev0[slot], h->stream);
+    const bool timed = h->prof_on && (h->prof_count++ % h->prof_every) == 0;
+    const size_t slot = timed ? prof_slot(h) : 0;
+    if (timed) cudaEventRecord(h->ev0[slot], h->stream);
     int kind = resolve_kind(h);
     if (io.obj && kind != LBM_KERNEL_CELL) kind = LBM_KERNEL_PAIR;   // the kernel that sums the objective
     cudaError_t err = cudaSuccess;
@@ -678,7 +681,7 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
         if (io.stats) lbmk::step_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
         else lbmk::step_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
     }
-    if (h->prof_on) cudaEventRecord(h->ev1[slot], h->stream);
+    if (timed) cudaEventRecord(h->ev1[slot], h->stream);
     h->launches += 1;
     return err;
 }
@@ -1283,7 +1286,7 @@ int lbm_wall_shear_noalloc(lbm_handle *h, double *out) {
 }
 
 int lbm_profile_enable(lbm_handle *h, int on) {
-    if (!h) return LBM_EINVAL;
+    if (!h || on < 0) return LBM_EINVAL;
     if (on && h->ev0.empty()) {
         h->ev0.resize(kEventPool); h->ev1.resize(kEventPool); h->ev_busy.assign(kEventPool, 0);
         for (size_t c = 0; c < kEventPool; ++c) {
@@ -1292,6 +1295,8 @@ int lbm_profile_enable(lbm_handle *h, int on) {
         }
     }
     h->prof_on = on != 0;
+    h->prof_every = on > 0 ? on : 1;
+    h->prof_count = 0;
     return LBM_OK;
 }
 

@@ -110,6 +110,16 @@ def test_step_kernel_selection_is_checked_on_the_host():
     lib.lbm_destroy(h)
 
 
+def test_profiling_interval_is_checked_on_the_host():
+    lib = _abi.lib()
+    rc, h = _create(nx=16)
+    assert rc == 0
+    assert lib.lbm_profile_enable(h, -1) == _abi.LBM_EINVAL
+    assert lib.lbm_profile_enable(None, 1) == _abi.LBM_EINVAL
+    assert lib.lbm_profile_enable(h, 0) == 0
+    lib.lbm_destroy(h)
+
+
 def test_checkpoint_calls_refuse_before_binding():
     lib = _abi.lib()
     rc, h = _create()
