@@ -218,9 +218,13 @@ int lbm_inlet_velocity(lbm_handle *h, long t, double *out);
  * steps 1-3 (eq:u_couple, eq:cholesky).  U[j]: streamwise mean velocity of
  * row j; R[6*j + c] = (R11, R22, R33, R12, R13, R23) of row j, lattice units.
  * set copies the host buffers, recomputes amp * chol(R) in FP64 on the host
- * and enqueues the upload on the stream (no synchronization); it returns
- * LBM_EINVAL if some R(j) is not positive definite.  The defaults are the
- * Reichardt profile and the analytic stress of lbm_create. */
+ * and uploads the result into the device profile buffer not in use, on a
+ * copy stream of the handle, so that the upload overlaps the steps in flight;
+ * the handle's stream waits for it before the next step (no host
+ * synchronization, except when the staging buffer of two calls ago is still
+ * being copied).  It returns LBM_EINVAL if some R(j) is not positive
+ * definite.  The defaults are the Reichardt profile and the analytic stress
+ * of lbm_create. */
 int lbm_set_inlet_profile(lbm_handle *h, const double *U, const double *R);
 int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R);
 
@@ -229,9 +233,12 @@ int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R);
 int lbm_wall_shear(lbm_handle *h, double *out);
 
 /* The same reduction enqueued without synchronizing: out (2*nx doubles,
- * owned by the caller, pinned host memory for the copy to be asynchronous)
- * holds the result once the handle's stream has passed this point (after
- * lbm_sync, a stream synchronize, or an event recorded after this call).
+ * owned by the caller) holds the result once the handle's stream has passed
+ * this point (after lbm_sync, a stream synchronize, or an event recorded after
+ * this call).  Page-locked host memory the device can address (cudaHostAlloc,
+ * a registered range) is written by the reduction kernel itself; any other
+ * memory gets a copy from device scratch on the stream (synchronous for
+ * pageable memory).
  * Successive calls are stream-ordered, so two output buffers used in turn let
  * a coupling loop read step n while step n + 1 runs.  Errors: LBM_EINVAL,
  * LBM_ESTATE before lbm_bind_memory, LBM_ECUDA. */

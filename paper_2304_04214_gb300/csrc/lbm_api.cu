@@ -117,7 +117,9 @@ struct lbm_handle {
     float *d_utau = nullptr, *d_fw = nullptr, *d_uin = nullptr, *d_ubuf = nullptr;
     double *d_st = nullptr, *d_st_utau = nullptr;
     unsigned *d_flags = nullptr;
-    float *d_UR = nullptr, *d_amat = nullptr;
+    float *d_UR = nullptr, *d_amat = nullptr;   // inlet profile in use (one of the two buffers)
+    float *d_prof = nullptr;                    // two buffers of 7 ny floats: U_R[ny], amp chol(R)[ny][6]
+    int prof_cur = 0;                           // the buffer in use
     float4 *d_sqsig = nullptr;
     uint32_t *d_alpha = nullptr, *d_betaT = nullptr, *d_phi32 = nullptr;
     // STG ring, two halves of stg_ring time levels: the half in use holds the
@@ -145,6 +147,8 @@ struct lbm_handle {
     bool custom_profile = false;
     std::vector<double> prof_U, prof_R;
     double *d_tw = nullptr;                // [2][nx] wall-shear scratch
+    bool fw_side = false;                  // d_fw was last written by the side-stream wall kernel
+    cudaEvent_t ev_shear = nullptr;        // wall-shear reduction done on the side stream
     // the wall-row kernel runs beside the interior kernel on a side stream,
     // forked from and joined back into the handle's stream every step
     cudaStream_t side = nullptr;
@@ -152,8 +156,13 @@ struct lbm_handle {
     // a second side stream for the STG work of lbm_adjoint_step
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_aux_fork = nullptr, ev_aux_join = nullptr;
-    float *pin_stage = nullptr;            // pinned staging of U_R and amp*chol(R): 7*ny floats
-    cudaEvent_t stage_ev = nullptr;        // last upload from the staging buffer
+    // inlet profile uploads (lbm_set_inlet_profile): pinned staging of U_R and
+    // amp chol(R), one half per device buffer, copied on their own stream;
+    // ev_prof_ready[b]: the upload into buffer b is done (and its staging half
+    // free); ev_prof_free[b]: the steps that read buffer b are done
+    float *pin_stage = nullptr;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_prof_ready[2] = {nullptr, nullptr}, ev_prof_free[2] = {nullptr, nullptr};
     // instrumentation
     bool prof_on = false;
     int prof_every = 1;                    // time every prof_every-th step launch
@@ -181,7 +190,8 @@ struct lbm_handle {
         d_st_utau = ar.take<double>(2 * (size_t)nx);
         d_tw = ar.take<double>(2 * (size_t)nx);
         d_flags = ar.take<unsigned>(4);
-        d_UR = ar.take<float>(7 * (size_t)ny);    // U_R[ny], then amp * chol(R)[ny][6]
+        d_prof = ar.take<float>(14 * (size_t)ny);
+        d_UR = d_prof + 7 * (size_t)ny * prof_cur;
         d_amat = d_UR + ny;
         d_sqsig = ar.take<float4>((size_t)ny * N);
         d_alpha = ar.take<uint32_t>((size_t)ny * N);
@@ -641,6 +651,7 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
     if (timed) cudaEventRecord(h->ev0[slot], h->stream);
     int kind = resolve_kind(h);
     if (io.obj && kind != LBM_KERNEL_CELL) kind = LBM_KERNEL_PAIR;   // the kernel that sums the objective
+    if (io.fw == h->d_fw) h->fw_side = kind != LBM_KERNEL_CELL;
     cudaError_t err = cudaSuccess;
     if (kind == LBM_KERNEL_STAGED || kind == LBM_KERNEL_PAIR || kind == LBM_KERNEL_QUAD) {
         // the wall rows on the side stream, the interior rows on the handle's
@@ -931,8 +942,12 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
     h->mem_bytes = need;
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-    if (cudaHostAlloc((void **)&h->pin_stage, 7 * sizeof(float) * h->ny, cudaHostAllocDefault) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess ||
+    if (cudaHostAlloc((void **)&h->pin_stage, 14 * sizeof(float) * h->ny, cudaHostAllocDefault) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_prof_ready[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_prof_ready[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_prof_free[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_prof_free[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -940,7 +955,8 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
         cudaEventCreateWithFlags(&h->ev_aux_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_aux_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_stg_free, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_stg_ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_stg_ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_shear, cudaEventDisableTiming) != cudaSuccess) {
         if (h->owns) cudaFree(h->mem);
         h->mem = nullptr;
         return cuda_fail(cudaGetLastError());
@@ -1195,14 +1211,27 @@ int lbm_set_inlet_profile(lbm_handle *h, const double *U, const double *R) {
     h->custom_profile = true;
     if (!h->bound) return LBM_OK;
     cudaError_t e;
-    // the pinned staging buffer may still feed the previous upload
-    if ((e = cudaEventSynchronize(h->stage_ev)) != cudaSuccess) return cuda_fail(e);
-    std::copy(h->UR.begin(), h->UR.end(), h->pin_stage);
-    std::copy(h->amat.begin(), h->amat.end(), h->pin_stage + h->ny);
-    // d_UR and d_amat are one block of 7 ny floats: one copy
-    if ((e = cudaMemcpyAsync(h->d_UR, h->pin_stage, 7 * (size_t)h->ny * 4, cudaMemcpyHostToDevice,
-                             h->stream)) != cudaSuccess) return cuda_fail(e);
-    return cuda_fail(cudaEventRecord(h->stage_ev, h->stream));
+    // Double-buffered upload: the profile goes into the buffer not in use, on
+    // the copy stream, after the steps that last read that buffer (those
+    // before the previous call), so that it overlaps the steps in flight; the
+    // handle's stream waits for it before the next step.
+    const int b = h->prof_cur ^ 1;
+    const size_t n7 = 7 * (size_t)h->ny;
+    float *stage = h->pin_stage + n7 * b, *dst = h->d_prof + n7 * b;
+    // the staging half may still feed the upload of two calls ago
+    if ((e = cudaEventSynchronize(h->ev_prof_ready[b])) != cudaSuccess) return cuda_fail(e);
+    std::copy(h->UR.begin(), h->UR.end(), stage);
+    std::copy(h->amat.begin(), h->amat.end(), stage + h->ny);
+    if ((e = cudaStreamWaitEvent(h->copy, h->ev_prof_free[b], 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dst, stage, n7 * sizeof(float), cudaMemcpyHostToDevice, h->copy)) != cudaSuccess ||
+        (e = cudaEventRecord(h->ev_prof_ready[b], h->copy)) != cudaSuccess ||
+        (e = cudaEventRecord(h->ev_prof_free[h->prof_cur], h->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h->stream, h->ev_prof_ready[b], 0)) != cudaSuccess)
+        return cuda_fail(e);
+    h->prof_cur = b;
+    h->d_UR = dst;
+    h->d_amat = dst + h->ny;
+    return LBM_OK;
 }
 
 int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R) {
@@ -1216,9 +1245,9 @@ int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R) {
 
 // z-averaged wall shear of the last step into device memory out[2 * nx]
 // (every entry written).
-static void launch_wall_shear(lbm_handle *h, double *out) {
+static void launch_wall_shear(lbm_handle *h, double *out, cudaStream_t st) {
     const dim3 grid((h->nx + lbmk::WS_X - 1) / lbmk::WS_X, 2), block(lbmk::WS_X, lbmk::WS_Z);
-    lbmk::wall_shear_kernel<<<grid, block, 0, h->stream>>>(h->d_fw, out, h->nx, h->nz);
+    lbmk::wall_shear_kernel<<<grid, block, 0, st>>>(h->d_fw, out, h->nx, h->nz);
 }
 
 extern "C" {
@@ -1227,11 +1256,34 @@ int lbm_wall_shear_async(lbm_handle *h, double *out) {
     if (!h || !out) return LBM_EINVAL;
     if (!h->bound) return LBM_ESTATE;
     const int n = 2 * h->nx;
-    launch_wall_shear(h, h->d_tw);
+    // page-locked host memory the device can address: the reduction stores
+    // straight into it (no separate copy on the stream); other memory gets
+    // the device result copied
+    cudaPointerAttributes pa;
+    double *direct = nullptr;
+    if (cudaPointerGetAttributes(&pa, out) == cudaSuccess) {
+        if (pa.type == cudaMemoryTypeHost && pa.devicePointer) direct = static_cast<double *>(pa.devicePointer);
+    } else {
+        cudaGetLastError();                      // not a pointer CUDA knows: copy
+    }
+    // When the side-stream wall kernel wrote the forces, the reduction follows
+    // it there, beside the interior kernel of the same step; the handle's
+    // stream then waits for it, so it still precedes whatever the caller
+    // enqueues next (and the next step's wall kernel comes after it on the
+    // side stream).
+    const cudaStream_t st = h->fw_side ? h->side : h->stream;
+    launch_wall_shear(h, direct ? direct : h->d_tw, st);
     h->launches += 1;
     cudaError_t e;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-    return cuda_fail(cudaMemcpyAsync(out, h->d_tw, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (!direct &&
+        (e = cudaMemcpyAsync(out, h->d_tw, n * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if (st != h->stream &&
+        ((e = cudaEventRecord(h->ev_shear, st)) != cudaSuccess ||
+         (e = cudaStreamWaitEvent(h->stream, h->ev_shear, 0)) != cudaSuccess))
+        return cuda_fail(e);
+    return LBM_OK;
 }
 
 int lbm_wall_shear(lbm_handle *h, double *out) {
@@ -1277,7 +1329,7 @@ int lbm_wall_shear_noalloc(lbm_handle *h, double *out) {
     }
     const int n = 2 * h->nx;
     // every entry read below is written by this launch first
-    launch_wall_shear(h, scratch);
+    launch_wall_shear(h, scratch, h->stream);
     h->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemcpyAsync(out, scratch, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
@@ -1723,14 +1775,19 @@ int lbm_load(lbm_handle *h, const char *path) {
 void lbm_destroy(lbm_handle *h) {
     if (!h) return;
     // no work of the handle may still run when its memory goes
+    if (h->copy) cudaStreamSynchronize(h->copy);
     if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->side) cudaStreamSynchronize(h->side);
     if (h->adj.owns && h->adj.mem) { cudaStreamSynchronize(h->stream); cudaFree(h->adj.mem); }
     if (h->bound) cudaStreamSynchronize(h->stream);
     for (size_t c = 0; c < h->ev0.size(); ++c) { cudaEventDestroy(h->ev0[c]); cudaEventDestroy(h->ev1[c]); }
     if (h->owns && h->mem) cudaFree(h->mem);
+    if (h->copy) { cudaStreamSynchronize(h->copy); cudaStreamDestroy(h->copy); }
     if (h->pin_stage) cudaFreeHost(h->pin_stage);
-    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_prof_ready[b]) cudaEventDestroy(h->ev_prof_ready[b]);
+        if (h->ev_prof_free[b]) cudaEventDestroy(h->ev_prof_free[b]);
+    }
     if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -1739,6 +1796,7 @@ void lbm_destroy(lbm_handle *h) {
     if (h->ev_aux_join) cudaEventDestroy(h->ev_aux_join);
     if (h->ev_stg_free) cudaEventDestroy(h->ev_stg_free);
     if (h->ev_stg_ready) cudaEventDestroy(h->ev_stg_ready);
+    if (h->ev_shear) cudaEventDestroy(h->ev_shear);
     delete h;
 }
 
