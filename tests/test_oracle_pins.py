@@ -301,6 +301,49 @@ def test_stg_tables_structure():
     assert np.allclose(t["kn"][1:] / t["kn"][:-1], 1.01, rtol=1e-13)
 
 
+def test_stg_length_scale_limits():
+    """Reading A16 (iii): the energetic length scale is a smooth stand-in for
+    min(2 d_w, l_e delta): it follows twice the wall distance at the wall
+    (within 0.2% at the first cell) and saturates at l_e delta in the core
+    (within 0.1%), growing monotonically in between, and is symmetric about
+    the centre line."""
+    ny, le = 96, 0.4
+    o = _stg(ny=ny, N=16, theta=(le, 1.0, 0.4, 7.8))
+    ell = o.tables()["ell"]
+    delta = ny / 2
+    y = np.arange(ny) + 0.5
+    d = np.minimum(y, ny - y)
+    assert abs(ell[0] / (2 * d[0]) - 1.0) < 2e-3
+    assert abs(ell[ny // 2] / (le * delta) - 1.0) < 1e-3
+    assert np.all(np.diff(ell[: ny // 2]) > 0)
+    assert np.allclose(ell, ell[::-1], rtol=0, atol=1e-12)
+    assert np.all(ell <= np.minimum(2 * d, le * delta) * (1 + 1e-12))
+
+
+def test_stg_spectrum_has_no_energy_past_the_kolmogorov_scale():
+    """Reading A16 (ii): the Kolmogorov factor removes the modes finer than
+    the dissipation scale.  At Re_tau = 100 on 96 cells the Kolmogorov
+    wavenumber k_eta = 2 pi (eps / nu^3)^(1/4), eps = u_tau^3 / (kappa d_w),
+    falls inside the resolved range in the core; the modes with
+    k_eta / 3 < k < 0.9 pi (below the grid cut-off) carry less than 1e-6 of
+    the energy there, where the bare von Karman shape puts over 1%."""
+    ny = 96
+    o = _stg(ny=ny, N=400, re_tau=100.0)
+    t, c = o.tables(), o.constants()
+    k = t["kn"]
+    j = 40
+    d = j + 0.5
+    keta = 2 * math.pi * (c["utau_ref"] ** 3 / (0.4 * d) / c["nu"] ** 3) ** 0.25
+    fine = (k > keta / 3) & (k < 0.9 * math.pi)     # resolved, before the grid cut-off
+    assert fine.sum() > 20
+    assert (t["sqrtq"][j, fine] ** 2).sum() < 1e-6
+    # the von Karman shape alone puts a visible share there
+    ke = 2 * math.pi / t["ell"][j]
+    r = k / ke
+    vk = r ** 4 / (1 + 2.4 * r * r) ** (17 / 6) * k
+    assert vk[fine].sum() / vk[k < 0.9 * math.pi].sum() > 0.01
+
+
 def test_stg_spectrum_shape():
     """Modified von Karman spectrum: E ~ k^4 well below k_e, ~ k^(-5/3) well
     above it (before the cut-offs), peak at k = k_e."""
