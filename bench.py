@@ -49,6 +49,17 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest x over the ranks (a job's time is its slowest rank's);
+    x itself on one rank."""
+    if ws == 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -264,10 +275,7 @@ def run_native(args, cfg, ws, rank, local):
     lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))
     lib.lbm_profile_enable(h, 0)
     ch.sync()
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, dev)
     value = ncell * ws * args.steps / (ms * 1e-3) / 1e6
 
     # ---- roofline of the fused step kernel ----
@@ -311,10 +319,7 @@ def run_native(args, cfg, ws, rank, local):
     taken.append(float(tws[(n_e2e - 1) % 2][0]))
     barrier()
     dt_e2e = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([dt_e2e], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt_e2e = float(t.item())
+    dt_e2e = max_over_ranks(dt_e2e, ws, dev)
     e2e = ncell * ws * n_e2e / dt_e2e / 1e6
     assert len(taken) == n_e2e and np.all(np.isfinite(taken)) and np.all(np.isfinite(tws[0].numpy()))
     ch.sync()
