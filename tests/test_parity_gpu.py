@@ -143,14 +143,24 @@ def test_statistics_accumulate_like_the_oracle():
     assert np.max(np.abs(utg - uto)) < 1e-5 * np.max(uto)
 
 
-def test_full_size_re_tau_1000_channel_first_steps():
-    """384x96x96 (Re_tau = 1000, N = 200): the bench workload and launch
-    configuration, compared over the whole lattice after two steps."""
-    o, g = make_pair(384, 96, 96, n_modes=200, seed=2)
+@pytest.mark.parametrize("shape,re_tau,n_modes,seed,precision,tol", [
+    ((384, 96, 96), 1000.0, 200, 2, "fp32", 1e-5),
+    ((384, 96, 96), 1000.0, 200, 2, "fp16", 2e-3),
+    ((768, 128, 192), 2000.0, 300, 3, "fp32", 1e-5),
+    ((768, 128, 192), 2000.0, 300, 3, "fp16", 2e-3),
+])
+def test_full_size_channels_first_steps(shape, re_tau, n_modes, seed, precision, tol):
+    """The bench workloads 384x96x96 (Re_tau = 1000, N = 200) and 768x128x192
+    (Re_tau = 2000, N = 300) in the launch configuration bench.py times (the
+    automatic kernel choice: two cells per thread for FP32, four for FP16;
+    the wall kernel's plane walk), compared over the whole lattice after two
+    steps."""
+    o, g = make_pair(*shape, re_tau=re_tau, n_modes=n_modes, seed=seed, precision=precision)
     o.step(2)
     g.step(2)
     er, eu = field_errors(o, g)
-    assert er < 1e-5 and eu < 1e-5, (er, eu)
+    assert er < tol and eu < tol, (er, eu)
+    g.close()
 
 
 def test_divergence_is_reported():
