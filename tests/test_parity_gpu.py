@@ -143,6 +143,28 @@ def test_statistics_accumulate_like_the_oracle():
     assert np.max(np.abs(utg - uto)) < 1e-5 * np.max(uto)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16", 2e-3)])
+def test_wall_plane_walk_with_a_ragged_last_block(precision, tol):
+    """Lattices whose interior kernel takes long enough make each wall-kernel
+    block walk several z planes (two here: 256x64x67 in FP32, 384x96x65 in
+    FP16); the odd nz leaves the last block a partial walk.  Fields and the
+    statistics, sampled every step (the statistics variants of the kernels),
+    against the oracle after two steps."""
+    shape = (256, 64, 67) if precision == "fp32" else (384, 96, 65)
+    o, g = make_pair(*shape, n_modes=32, seed=12, precision=precision, stats=1)
+    o.step(2)
+    g.step(2)
+    er, eu = field_errors(o, g)
+    assert er < tol and eu < tol, (er, eu)
+    so, uto, no = o.stats()
+    sg, utg, ng = g.stats()
+    assert no == ng == 2
+    for c in range(7):
+        assert np.max(np.abs(sg[..., c] - so[..., c])) < tol * np.max(np.abs(so[..., c])) + 1e-12, c
+    assert np.max(np.abs(utg - uto)) < tol * np.max(uto)
+    g.close()
+
+
 @pytest.mark.parametrize("shape,re_tau,n_modes,seed,precision,tol", [
     ((384, 96, 96), 1000.0, 200, 2, "fp32", 1e-5),
     ((384, 96, 96), 1000.0, 200, 2, "fp16", 2e-3),
