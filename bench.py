@@ -242,6 +242,7 @@ def run_native(args, cfg, ws, rank, local):
     ch = LBMChannel(nx, ny, nz, re_tau=cfg["re_tau"], n_modes=cfg["n_modes"],
                     seed=cfg["seed"] + 1000 * rank, precision=args.precision,
                     stats_every=STATS_EVERY, step_kernel=args.kernel, device=dev)
+    ch.set_graphs(args.graphs == "on")
     lib, h = ch.lib, ch.h
     kernel = ch.step_kernel
     stream = torch.cuda.current_stream(dev)
@@ -257,10 +258,11 @@ def run_native(args, cfg, ws, rank, local):
     barrier()
 
     # ---- timed region: K steps, device events, kernel events, clocks ----
-    # the step kernels of every PROF_EVERY-th step are bracketed by events on
-    # the library's stream (an event pair costs the stream a few us, so
-    # timing every step would inflate the step it measures)
-    _abi.check(lib.lbm_profile_enable(h, PROF_EVERY), "lbm_profile_enable")
+    # events on the library's stream bracket each graph launch (64 steps) and
+    # the kernels of every timed_every-th separately launched step (an event
+    # pair costs the stream a few us, so timing every step would inflate the
+    # step it measures)
+    _abi.check(lib.lbm_profile_enable(h, args.timed_every), "lbm_profile_enable")
     ms_k, nk, nall = ct.c_double(), ct.c_long(), ct.c_long()
     lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))   # reset counters
     e0 = torch.cuda.Event(enable_timing=True)
@@ -346,13 +348,17 @@ def run_native(args, cfg, ws, rank, local):
                        "stats_every": STATS_EVERY,
                        "l2": "no flush: the two lattices (%.0f MB) exceed the 129 MB L2"
                              % (2 * BYTES_PER_CELL[args.precision] / 2 * ncell / 1e6),
-                       "parallelism": "replicas" if ws > 1 else "single"},
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "cuda_graphs": args.graphs == "on"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(achieved / peaks["hbm_gbs"], 4),
                          "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": KERNEL_NAMES[kernel], "kernel_ms": round(kern_ms, 5),
-                         "timed_launches": nk.value, "timed_every": PROF_EVERY,
+                         "kernel": KERNEL_NAMES[kernel] + (
+                             " (64-step CUDA graphs: the step kernels with the statistics and the"
+                             " ring refill, per step)" if args.graphs == "on" else ""),
+                         "kernel_ms": round(kern_ms, 5),
+                         "timed_steps": nk.value, "timed_every": args.timed_every,
                          "algorithmic_bytes": alg_bytes},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e, 1), "unit": "MLUPS",
@@ -413,6 +419,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "quad", "staged"])
+    ap.add_argument("--graphs", default="on", choices=["on", "off"],
+                    help="launch STG ring periods of steps as CUDA graphs")
+    ap.add_argument("--timed-every", type=int, default=PROF_EVERY,
+                    help="bracket the step kernels of every n-th step with CUDA events")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -118,8 +118,22 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes);
  * without synchronizing.  Each step: inlet velocity (steps 4-5), then one
  * fused kernel doing pull streaming with the boundary rules, the regularized
  * inlet (steps 6-8), the wall model (steps 9-14) and the collision (step 15).
+ * With CUDA graphs on (the default, lbm_set_graphs), whole periods of the STG
+ * ring (64 steps where the inlet plane allows) that fit in n are launched as
+ * one graph each, built the first time a period's launch state occurs; the
+ * steps and their results are the same as with separate launches.
  * Errors: LBM_ESTATE before lbm_bind_memory, LBM_EINVAL if n < 0, LBM_ECUDA. */
 int lbm_step(lbm_handle *h, int n);
+
+/* Launch ring periods of steps as CUDA graphs (on != 0, the default) or every
+ * kernel separately (on = 0).  Errors: LBM_EINVAL. */
+int lbm_set_graphs(lbm_handle *h, int on);
+
+/* Whether graphs are on (*on; 0 also after a capture the runtime refused),
+ * and how many graph launches lbm_step has made (*launched; each also
+ * launches one single-thread kernel that sets the period's start time, which
+ * the launch counts of lbm_profile_read include).  Errors: LBM_EINVAL. */
+int lbm_graph_info(const lbm_handle *h, int *on, long *launched);
 
 /* Synchronize the stream and report deferred device errors:
  * LBM_EDIVERGED, LBM_ENOTCONV, LBM_ETIMEOUT (the counters are cleared when
@@ -269,14 +283,15 @@ int lbm_wall_shear_async(lbm_handle *h, double *out);
 #define LBM_NOALLOC_MAX_NX 32768
 int lbm_wall_shear_noalloc(lbm_handle *h, double *out);
 
-/* Instrumentation.  While enabled (on > 0), every on-th launch of the fused
- * step kernel (interior and wall rows, from the first one after the call) is
+/* Instrumentation.  While enabled (on > 0), every on-th separately launched
+ * step (interior and wall-row kernels, from the first one after the call) is
  * bracketed by CUDA events on the handle's stream: on = 1 times every step,
  * a larger on samples them (each event pair costs the stream a few
- * microseconds).  on = 0 disables; on < 0 is LBM_EINVAL.  read synchronizes
- * and returns the summed kernel time in ms and the number of timed launches
- * since the last read, and the number of kernels of any kind the handle
- * launched. */
+ * microseconds); a graph of a ring period (lbm_step) is bracketed as a whole
+ * and counts for its steps (their kernels, the statistics reductions and the
+ * ring refill).  on = 0 disables; on < 0 is LBM_EINVAL.  read synchronizes
+ * and returns the summed time in ms and the number of timed steps since the
+ * last read, and the number of kernels of any kind the handle launched. */
 int lbm_profile_enable(lbm_handle *h, int on);
 int lbm_profile_read(lbm_handle *h, double *ms_total, long *step_launches, long *all_launches);
 

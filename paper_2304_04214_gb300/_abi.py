@@ -59,6 +59,8 @@ PROTOTYPES = {
     "lbm_save": (ct.c_int, [_h, ct.c_char_p]),
     "lbm_load": (ct.c_int, [_h, ct.c_char_p]),
     "lbm_set_step_kernel": (ct.c_int, [_h, ct.c_int]),
+    "lbm_set_graphs": (ct.c_int, [_h, ct.c_int]),
+    "lbm_graph_info": (ct.c_int, [_h, ct.POINTER(ct.c_int), ct.POINTER(ct.c_long)]),
     "lbm_get_step_kernel": (ct.c_int, [_h, ct.POINTER(ct.c_int)]),
     "lbm_set_sponge": (ct.c_int, [_h, ct.c_int, ct.c_double]),
     "lbm_stats": (ct.c_int, [_h, _dp, _dp, ct.POINTER(ct.c_long)]),

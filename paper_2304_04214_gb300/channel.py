@@ -111,6 +111,16 @@ class LBMChannel:
     def step_kernel(self, name):
         _abi.check(self.lib.lbm_set_step_kernel(self.h, _abi.KERNELS[name]), "lbm_set_step_kernel")
 
+    def set_graphs(self, on):
+        """Launch ring periods of steps as CUDA graphs (default) or not."""
+        _abi.check(self.lib.lbm_set_graphs(self.h, int(bool(on))), "lbm_set_graphs")
+
+    def graph_info(self):
+        """(graphs on, graph launches so far)."""
+        on, n = ct.c_int(), ct.c_long()
+        _abi.check(self.lib.lbm_graph_info(self.h, ct.byref(on), ct.byref(n)), "lbm_graph_info")
+        return bool(on.value), n.value
+
     def set_sponge(self, cells, nu_max):
         """Outlet sponge: over the last `cells` cells the viscosity rises by
         nu_max r^2 (r the position in the zone); cells = 0 switches it off."""

@@ -147,6 +147,7 @@ struct lbm_handle {
     bool custom_profile = false;
     std::vector<double> prof_U, prof_R;
     double *d_tw = nullptr;                // [2][nx] wall-shear scratch
+    long long *d_gt0 = nullptr;            // start time of the refill inside a graph
     bool fw_side = false;                  // d_fw was last written by the side-stream wall kernel
     cudaEvent_t ev_shear = nullptr;        // wall-shear reduction done on the side stream
     // the wall-row kernel runs beside the interior kernel on a side stream,
@@ -167,8 +168,23 @@ struct lbm_handle {
     bool prof_on = false;
     int prof_every = 1;                    // time every prof_every-th step launch
     long long prof_count = 0;
+    // CUDA graphs of one STG ring period of steps (lbm_step, see graph_segment)
+    struct GraphSeg {
+        long long key[9];                  // launch-relevant host state at the segment start
+        cudaGraphExec_t exec = nullptr;
+        long long d_launches = 0, after_since_stats = 0, d_samples = 0;
+    };
+    std::vector<GraphSeg> graphs;
+    bool graphs_on = true;
+    bool capturing = false;
+    long long graph_launches = 0;
+    long long graph_epoch = 0, graphs_built_epoch = 0;
+    cudaStream_t gstream = nullptr;        // capture stream
+    // fork / join of the refill inside a graph (events recorded in a capture
+    // are waited on only inside it)
+    cudaEvent_t ev_gfork = nullptr, ev_gjoin = nullptr;
     std::vector<cudaEvent_t> ev0, ev1;
-    std::vector<char> ev_busy;
+    std::vector<int> ev_busy;              // steps a busy slot times (0: free)
     size_t ev_next = 0;
     double prof_ms = 0;
     long prof_n = 0, launches = 0;
@@ -189,6 +205,7 @@ struct lbm_handle {
         d_st = ar.take<double>(7 * (size_t)nx * ny);
         d_st_utau = ar.take<double>(2 * (size_t)nx);
         d_tw = ar.take<double>(2 * (size_t)nx);
+        d_gt0 = ar.take<long long>(1);
         d_flags = ar.take<unsigned>(4);
         d_prof = ar.take<float>(14 * (size_t)ny);
         d_UR = d_prof + 7 * (size_t)ny * prof_cur;
@@ -456,6 +473,7 @@ struct lbm_handle {
         const size_t N = n_modes > 0 ? n_modes : 1;
         cudaError_t e;
         stg_reset();                            // the tables feed the ring
+        ++graph_epoch;                          // and the step parameters
 #define UP(dst, vec) if ((e = cudaMemcpyAsync(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return e
         UP(d_UR, UR); UP(d_amat, amat); UP(d_sqsig, sqsig);
         UP(d_alpha, alpha); UP(d_betaT, betaT); UP(d_phi32, phi32); UP(d_rate64, rate64);
@@ -482,7 +500,7 @@ void prof_harvest(lbm_handle *h, size_t slot) {
     cudaEventSynchronize(h->ev1[slot]);
     cudaEventElapsedTime(&ms, h->ev0[slot], h->ev1[slot]);
     h->prof_ms += ms;
-    h->prof_n += 1;
+    h->prof_n += h->ev_busy[slot];
     h->ev_busy[slot] = 0;
 }
 
@@ -646,9 +664,15 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
     a.obj = io.obj; a.obj_i0 = io.obj_i0; a.obj_i1 = io.obj_i1; a.obj_iR = io.obj_iR;
     sponge_args(h, a.sp_x0, a.sp_inv, a.sp_3nu);
     const int bxmax = lbmk::STEP_THREADS / lbmk::BY;
-    const bool timed = h->prof_on && (h->prof_count++ % h->prof_every) == 0;
-    const size_t slot = timed ? prof_slot(h) : 0;
-    if (timed) cudaEventRecord(h->ev0[slot], h->stream);
+    // (steps inside a graph are timed by events around the graph launch)
+    const bool timed = h->prof_on && !h->capturing && (h->prof_count++ % h->prof_every) == 0;
+    cudaEvent_t tev0 = nullptr, tev1 = nullptr;
+    if (timed) {
+        const size_t slot = prof_slot(h);
+        tev0 = h->ev0[slot];
+        tev1 = h->ev1[slot];
+    }
+    if (timed) cudaEventRecord(tev0, h->stream);
     int kind = resolve_kind(h);
     if (io.obj && kind != LBM_KERNEL_CELL) kind = LBM_KERNEL_PAIR;   // the kernel that sums the objective
     if (io.fw == h->d_fw) h->fw_side = kind != LBM_KERNEL_CELL;
@@ -692,7 +716,7 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
         if (io.stats) lbmk::step_kernel<S, true><<<grid, block, 0, h->stream>>>(a);
         else lbmk::step_kernel<S, false><<<grid, block, 0, h->stream>>>(a);
     }
-    if (timed) cudaEventRecord(h->ev1[slot], h->stream);
+    if (timed) cudaEventRecord(tev1, h->stream);
     h->launches += 1;
     return err;
 }
@@ -727,7 +751,7 @@ void launch_stg(lbm_handle *h, long long t0, int n, bool apply_profile) {
     lbmk::StgArgs a;
     a.alpha = h->d_alpha; a.betaT = h->d_betaT; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
     a.sqsig = h->d_sqsig; a.amat = h->d_amat; a.UR = h->d_UR; a.out = h->d_uin;
-    a.t0 = t0; a.nsteps = n; a.apply_profile = apply_profile ? 1 : 0;
+    a.t0 = t0; a.t0_dev = nullptr; a.nsteps = n; a.apply_profile = apply_profile ? 1 : 0;
     a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
     launch_stg_kernel(h, a, h->stream);
 }
@@ -788,6 +812,8 @@ void launch_stg_into(lbm_handle *h, float *out, long long t0, int n, cudaStream_
     a.alpha = h->d_alpha; a.betaT = h->d_betaT; a.phi32 = h->d_phi32; a.rate64 = h->d_rate64;
     a.sqsig = h->d_sqsig; a.amat = h->d_amat; a.UR = h->d_UR; a.out = out;
     a.t0 = t0; a.nsteps = n; a.apply_profile = 0;
+    // inside a graph the start time comes from device memory, set before every launch
+    a.t0_dev = h->capturing ? h->d_gt0 : nullptr;
     a.ny = h->ny; a.nz = h->nz; a.n_modes = h->n_modes;
     launch_stg_kernel(h, a, st);
 }
@@ -868,6 +894,157 @@ float bf16_to_f32(uint16_t v) {
     float x;
     std::memcpy(&x, &b, 4);
     return x;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of whole STG ring periods.  lbm_step launches the stg_ring steps
+// that start where the ring swaps halves as one graph: the steps of one
+// period, and beside them the refill of the other half, joined at the end.
+// The launch parameters of a step depend on the host state at its start
+// (lattice parity, ring half, phases of the checks and the statistics,
+// inlet-profile buffer), which form the graph's key; equal keys give equal
+// graphs except for the refill's start time, which the refill reads from
+// device memory set before every launch.  Changes of the tables, the sponge
+// or the kernel choice retire all graphs (graph_epoch).
+// ---------------------------------------------------------------------------
+void graph_key(const lbm_handle *h, long long key[9]) {
+    key[0] = h->stg_half;
+    key[1] = h->cur;
+    key[2] = h->t % h->check_every;
+    key[3] = h->t & 1;
+    key[4] = h->steps_since_stats;
+    key[5] = 0;                            // (timing brackets whole graph launches)
+    key[6] = 0;
+    key[7] = h->prof_cur;
+    key[8] = h->stg_ring;
+}
+
+bool graph_usable(const lbm_handle *h) {
+    if (!(h->graphs_on && h->opts.inlet && h->stg_ring >= 8 && h->stg_next_t0 >= 0 && h->t == h->stg_next_t0 &&
+          resolve_kind(h) != LBM_KERNEL_STAGED))
+        return false;
+    // not while the caller captures the handle's stream into a graph of its own
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st == cudaStreamCaptureStatusNone;
+}
+
+void graphs_clear(lbm_handle *h) {
+    if (!h->graphs.empty()) cudaStreamSynchronize(h->stream);   // none may still run
+    for (auto &g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    h->graphs_built_epoch = h->graph_epoch;
+}
+
+// Launch a graph on the handle's stream, its refill starting at the period
+// after this one (set in device memory first).  With instrumentation on, a
+// pair of events brackets the launch and is booked for the period's steps.
+cudaError_t graph_launch(lbm_handle *h, lbm_handle::GraphSeg &g) {
+    lbmk::set_time_kernel<<<1, 1, 0, h->stream>>>(h->d_gt0, h->stg_t0 + h->stg_ring);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    size_t slot = 0;
+    if (h->prof_on) {
+        slot = prof_slot(h);
+        h->ev_busy[slot] = h->stg_ring;
+        if ((e = cudaEventRecord(h->ev0[slot], h->stream)) != cudaSuccess) return e;
+    }
+    if ((e = cudaGraphLaunch(g.exec, h->stream)) != cudaSuccess) return e;
+    if (h->prof_on) e = cudaEventRecord(h->ev1[slot], h->stream);
+    return e;
+}
+
+// Capture one ring period as the handle would enqueue it, on a capture stream
+// standing in for the handle's stream, and record in g what the period does to
+// the host state.  On return the host state is as before the call
+// (graph_segment advances it when it launches the graph); false if the
+// capture did not succeed.
+bool graph_capture(lbm_handle *h, lbm_handle::GraphSeg &g) {
+    if (!h->gstream && cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (!h->ev_gfork && cudaEventCreateWithFlags(&h->ev_gfork, cudaEventDisableTiming) != cudaSuccess) return false;
+    if (!h->ev_gjoin && cudaEventCreateWithFlags(&h->ev_gjoin, cudaEventDisableTiming) != cudaSuccess) return false;
+    const long long t0 = h->t, cur0 = h->cur, since0 = h->steps_since_stats, samples0 = h->n_samples;
+    const long long prof0 = h->prof_count, launches0 = h->launches;
+    const cudaStream_t real = h->stream;
+    h->stream = h->gstream;
+    h->capturing = true;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        // the refill of the other half, beside this period's steps
+        ok = cudaEventRecord(h->ev_gfork, h->gstream) == cudaSuccess &&
+             cudaStreamWaitEvent(h->aux, h->ev_gfork, 0) == cudaSuccess;
+        if (ok) {
+            launch_stg_into(h, h->stg_slot(h->stg_half ^ 1), h->stg_t0 + h->stg_ring, h->stg_ring, h->aux);
+            ok = cudaEventRecord(h->ev_gjoin, h->aux) == cudaSuccess;
+        }
+        for (int s = 0; ok && s < h->stg_ring; ++s) ok = one_step(h) == LBM_OK;
+        if (ok) ok = cudaStreamWaitEvent(h->gstream, h->ev_gjoin, 0) == cudaSuccess;
+        const cudaError_t ee = cudaStreamEndCapture(h->gstream, &graph);
+        ok = ok && ee == cudaSuccess && graph != nullptr;
+    }
+    h->stream = real;
+    h->capturing = false;
+    if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    const long long launches1 = h->launches, since1 = h->steps_since_stats, samples1 = h->n_samples;
+    h->t = t0; h->cur = (int)cur0; h->steps_since_stats = since0; h->n_samples = samples0;
+    h->prof_count = prof0; h->launches = launches0;
+    if (!ok) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        return false;
+    }
+    // the launch enqueues the work the capture only recorded
+    g.d_launches = launches1 - launches0;
+    g.after_since_stats = since1;
+    g.d_samples = samples1 - samples0;
+    return true;
+}
+
+// One ring period from the ring swap on: from a graph (built at the first
+// period with this key).  Returns LBM_OK, or 1 if no graph could be built
+// (the caller then steps one at a time; the swap has been made).
+int graph_segment(lbm_handle *h) {
+    if (h->graphs_built_epoch != h->graph_epoch) graphs_clear(h);
+    cudaError_t e;
+    // swap to the other half, filled beside the previous period
+    if ((e = cudaStreamWaitEvent(h->stream, h->ev_stg_ready, 0)) != cudaSuccess) return cuda_fail(e);
+    h->stg_half ^= 1;
+    h->stg_t0 = h->t;
+    h->stg_len = h->stg_ring;
+    long long key[9];
+    graph_key(h, key);
+    lbm_handle::GraphSeg *g = nullptr;
+    for (auto &c : h->graphs)
+        if (std::equal(key, key + 9, c.key)) g = &c;
+    if (!g) {
+        if (h->graphs.size() >= 32) graphs_clear(h);
+        lbm_handle::GraphSeg ng;
+        std::copy(key, key + 9, ng.key);
+        if (!graph_capture(h, ng)) {
+            h->graphs_on = false;                // capture refused: plain launches from now on
+            h->stg_next_t0 = -1;                 // the refill was not enqueued
+            return 1;
+        }
+        h->graphs.push_back(ng);
+        g = &h->graphs.back();
+    }
+    if ((e = graph_launch(h, *g)) != cudaSuccess) return cuda_fail(e);
+    // the events the captured steps recorded stay inside the graph: those
+    // waited on later are recorded again, here on the handle's stream (the
+    // refill of the next half is complete with the graph)
+    if ((e = cudaEventRecord(h->ev_stg_ready, h->stream)) != cudaSuccess) return cuda_fail(e);
+    h->t += h->stg_ring;
+    h->cur ^= (h->stg_ring & 1);
+    h->steps_since_stats = g->after_since_stats;
+    h->n_samples += g->d_samples;
+    h->prof_count += h->stg_ring;
+    h->launches += g->d_launches + 1;            // and the time setter
+    h->stg_next_t0 = h->stg_t0 + h->stg_ring;
+    ++h->graph_launches;
+    return LBM_OK;
 }
 
 }  // namespace
@@ -985,9 +1162,15 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
 int lbm_step(lbm_handle *h, int n) {
     if (!h || n < 0) return LBM_EINVAL;
     if (!h->bound) return LBM_ESTATE;
-    for (int s = 0; s < n; ++s) {
-        int rc = one_step(h);
+    for (int s = 0; s < n;) {
+        if (graph_usable(h) && n - s >= h->stg_ring) {
+            const int rc = graph_segment(h);
+            if (rc == LBM_OK) { s += h->stg_ring; continue; }
+            if (rc != 1) return rc;
+        }
+        const int rc = one_step(h);
         if (rc) return rc;
+        ++s;
     }
     return LBM_OK;
 }
@@ -1020,6 +1203,20 @@ int lbm_set_step_kernel(lbm_handle *h, int kind) {
         default: return LBM_EINVAL;
     }
     h->step_kind = kind;
+    ++h->graph_epoch;
+    return LBM_OK;
+}
+
+int lbm_set_graphs(lbm_handle *h, int on) {
+    if (!h) return LBM_EINVAL;
+    h->graphs_on = on != 0;
+    return LBM_OK;
+}
+
+int lbm_graph_info(const lbm_handle *h, int *on, long *launched) {
+    if (!h || !on || !launched) return LBM_EINVAL;
+    *on = h->graphs_on ? 1 : 0;
+    *launched = (long)h->graph_launches;
     return LBM_OK;
 }
 
@@ -1033,6 +1230,7 @@ int lbm_set_sponge(lbm_handle *h, int cells, double nu_max) {
     if (!h || cells < 0 || cells > h->nx || !(nu_max >= 0.0) || !std::isfinite(nu_max)) return LBM_EINVAL;
     h->sponge_cells = nu_max > 0.0 ? cells : 0;
     h->sponge_nu = cells > 0 ? nu_max : 0.0;
+    ++h->graph_epoch;
     return LBM_OK;
 }
 
@@ -1765,6 +1963,7 @@ int lbm_load(lbm_handle *h, const char *path) {
     }
     h->sponge_cells = hd.sponge_cells;
     h->sponge_nu = hd.sponge_nu;
+    ++h->graph_epoch;
     h->t = hd.t;
     h->n_samples = (long)hd.n_samples;
     h->steps_since_stats = hd.steps_since_stats;
@@ -1797,6 +1996,10 @@ void lbm_destroy(lbm_handle *h) {
     if (h->ev_stg_free) cudaEventDestroy(h->ev_stg_free);
     if (h->ev_stg_ready) cudaEventDestroy(h->ev_stg_ready);
     if (h->ev_shear) cudaEventDestroy(h->ev_shear);
+    graphs_clear(h);
+    if (h->ev_gfork) cudaEventDestroy(h->ev_gfork);
+    if (h->ev_gjoin) cudaEventDestroy(h->ev_gjoin);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     delete h;
 }
 

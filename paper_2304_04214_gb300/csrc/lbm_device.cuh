@@ -1109,9 +1109,13 @@ struct StgArgs {
     const float *__restrict__ UR;         // [ny] mean profile
     float *__restrict__ out;              // [nsteps][nz][ny][3]: v', or u_in if apply_profile
     long long t0;                         // time of slot 0
+    const long long *t0_dev;              // if set, the time of slot 0 is read here (graph replays)
     int nsteps, ny, nz, n_modes;
     int apply_profile;
 };
+
+// The one value a graph replay needs that differs between its launches.
+__global__ void set_time_kernel(long long *dst, long long v) { *dst = v; }
 
 constexpr int STG_KZ = 32, STG_KT = 8, STG_MCHUNK = 256;
 
@@ -1128,6 +1132,7 @@ __global__ void __launch_bounds__(STG_KZ * STG_KT) stg_kernel(const __grid_const
     const int lz = threadIdx.x % STG_KZ, lt0 = (threadIdx.x / STG_KZ) * TT;
     const int k = blockIdx.x * STG_KZ + lz;
     const int N = a.n_modes;
+    const long long t0 = a.t0_dev ? *a.t0_dev : a.t0;
     float vx[TT], vy[TT], vz[TT];
 #pragma unroll
     for (int tt = 0; tt < TT; ++tt) vx[tt] = vy[tt] = vz[tt] = 0.0f;
@@ -1136,7 +1141,7 @@ __global__ void __launch_bounds__(STG_KZ * STG_KT) stg_kernel(const __grid_const
         __syncthreads();
         for (int e = threadIdx.x; e < NT * nc; e += blockDim.x) {
             const int m = e / NT, tl = e % NT, n = n0 + m;
-            const uint64_t t = (uint64_t)(a.t0 + (long long)blockIdx.z * NT + tl);
+            const uint64_t t = (uint64_t)(t0 + (long long)blockIdx.z * NT + tl);
             s_ph[m][tl] = a.alpha[(size_t)j * N + n] + a.phi32[n] + (uint32_t)((a.rate64[n] * t) >> 32);
         }
         for (int e = threadIdx.x; e < nc; e += blockDim.x) s_sq[e] = a.sqsig[(size_t)j * N + n0 + e];
