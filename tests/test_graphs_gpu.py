@@ -98,3 +98,25 @@ def test_graph_replays_keep_the_instrumentation_counts():
     _same(a, b)
     a.close()
     b.close()
+
+
+def test_adjoint_windows_between_graph_periods():
+    """An adjoint window (its own forward steps, checkpoints and the STG work
+    on the second stream) between graph periods: J, dJ/dtheta (to the
+    rounding of its atomic sums) and the state after the steps that follow are
+    the same as without graphs."""
+    a, b = _pair("fp32")
+    out = []
+    for c in (a, b):
+        c.step(200)
+        J, dJ = c.adjoint_step(64, 8, (24, 48, 40))
+        c.step(200)
+        out.append((J, dJ))
+    # J from the same forward states; dJ/dtheta sums FP64 atomics, whose
+    # order varies from run to run
+    assert out[0][0] == out[1][0]
+    assert np.allclose(out[0][1], out[1][1], rtol=1e-9, atol=0)
+    assert a.graph_info()[1] >= 4
+    _same(a, b)
+    a.close()
+    b.close()
