@@ -84,6 +84,15 @@ MUTANTS = [
     ("length_scale_without_wall_limit",
      "h->ell[j] = le * delta * tanh(2.0 * d / (le * delta));",
      "h->ell[j] = le * delta;"),
+    ("stg_time_scale_with_k_squared",
+     "real xp = (x - h->c.u_bulk * (double)t) * 2.0 * PI_D / (kn * h->maxl);",
+     "real xp = (x - h->c.u_bulk * (double)t) * 2.0 * PI_D / (kn * kn * h->maxl);"),
+    ("stg_convection_without_u_bulk",
+     "real xp = (x - h->c.u_bulk * (double)t) * 2.0 * PI_D / (kn * h->maxl);",
+     "real xp = (x - (double)t) * 2.0 * PI_D / (kn * h->maxl);"),
+    ("stg_direction_components_swapped",
+     "real arg = kn * (d[0] * xp + d[1] * y + d[2] * z) + h->phin[n];",
+     "real arg = kn * (d[1] * xp + d[0] * y + d[2] * z) + h->phin[n];"),
     ("sponge_linear_ramp",
      "t0c = tau0 + 3.0 * h->c.sponge_nu * ramp * ramp;",
      "t0c = tau0 + 3.0 * h->c.sponge_nu * ramp;"),

@@ -344,6 +344,30 @@ def test_stg_spectrum_has_no_energy_past_the_kolmogorov_scale():
     assert vk[fine].sum() / vk[k < 0.9 * math.pi].sum() > 0.01
 
 
+def test_stg_inlet_signal_has_the_convective_frequencies():
+    """Reading A16 (iv): the modes are frozen patterns convected through the
+    inlet plane, x'_n = (x - U_b t) 2 pi / (k_n max l_e), so at x = 0 mode n
+    oscillates in time at f_n = |d_n,x| U_b / max l_e cycles per step,
+    whatever its wavenumber.  With three modes the velocity at one cell is a
+    constant plus three tones: a least-squares fit on those frequencies
+    leaves no residual (a missing U_b, a wrong time scale or a wrong
+    component of d_n would)."""
+    ny, nz, N, T = 32, 4, 3, 6000
+    o = _stg(ny=ny, nz=nz, N=N)
+    t, c = o.tables(), o.constants()
+    f = np.abs(t["dn"][:, 0]) * 0.05 / c["maxl"]
+    assert np.all(f * T > 10)                 # many periods in the record
+    x = np.array([o.inlet_velocity(s)[1, 9, 0] for s in range(T)])
+    ts = np.arange(T)
+    basis = np.concatenate([np.ones((T, 1))] +
+                           [np.stack([np.cos(2 * math.pi * fn * ts), np.sin(2 * math.pi * fn * ts)], 1)
+                            for fn in f], axis=1)
+    x = x - x.mean()
+    coef, *_ = np.linalg.lstsq(basis, x, rcond=None)
+    resid = x - basis @ coef
+    assert np.sum(resid ** 2) < 1e-20 * np.sum(x ** 2)
+
+
 def test_stg_spectrum_shape():
     """Modified von Karman spectrum: E ~ k^4 well below k_e, ~ k^(-5/3) well
     above it (before the cut-offs), peak at k = k_e."""
