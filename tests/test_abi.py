@@ -129,3 +129,19 @@ def test_checkpoint_calls_refuse_before_binding():
     assert lib.lbm_save(h, None) == _abi.LBM_EINVAL
     assert lib.lbm_save(None, b"x") == _abi.LBM_EINVAL
     lib.lbm_destroy(h)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/lbm.h is a C header: it compiles as C99 with warnings as
+    errors (no C++ in the boundary)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "lbm.h"\nint main(void) { return (int)sizeof(lbm_grid) > 0 ? 0 : 1; }\n')
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", inc, str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
