@@ -145,3 +145,29 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                         "-I", inc, str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("ny,re_tau", [(32, 1000.0), (96, 1000.0), (128, 2000.0), (192, 5200.0)])
+def test_host_constants_and_inlet_profile_match_the_oracle(ny, re_tau):
+    """The library's host-side set-up, computed at lbm_create without a GPU:
+    the flow constants (delta, u_tau,ref, nu, tau0, U_b+, max l_e) and the
+    default inlet profile -- the Reichardt mean U_R(y) and the prescribed
+    Reynolds stress R(y) in lattice units -- equal the oracle's, computed by
+    its own FP64 code (reading A20, eq:reichard, reading A16 vi)."""
+    from oracle.oracle import Oracle, default_config
+    lib = _abi.lib()
+    rc, h = _create(nx=16, ny=ny, nz=4, re_tau=re_tau)
+    assert rc == 0
+    dp = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_double))   # noqa: E731
+    cst = np.zeros(6)
+    assert lib.lbm_get_constants(h, dp(cst)) == 0
+    U, R = np.zeros(ny), np.zeros(6 * ny)
+    assert lib.lbm_get_inlet_profile(h, dp(U), dp(R)) == 0
+    lib.lbm_destroy(h)
+    o = Oracle(default_config(16, ny, 4, re_tau=re_tau, n_modes=4),
+               uniforms=np.full((4, 4), 0.25))
+    oc, t = o.constants(), o.tables()
+    ref = [oc["delta"], oc["utau_ref"], oc["nu"], oc["tau0"], oc["ubp"], oc["maxl"]]
+    assert np.allclose(cst, ref, rtol=1e-12, atol=0), (cst, ref)
+    assert np.allclose(U, t["UR"], rtol=1e-12, atol=1e-15)
+    assert np.allclose(R.reshape(ny, 6), t["Rp"] * oc["utau_ref"] ** 2, rtol=1e-12, atol=1e-18)
