@@ -171,3 +171,37 @@ def test_host_constants_and_inlet_profile_match_the_oracle(ny, re_tau):
     assert np.allclose(cst, ref, rtol=1e-12, atol=0), (cst, ref)
     assert np.allclose(U, t["UR"], rtol=1e-12, atol=1e-15)
     assert np.allclose(R.reshape(ny, 6), t["Rp"] * oc["utau_ref"] ** 2, rtol=1e-12, atol=1e-18)
+
+
+def test_setters_validate_on_the_host():
+    """Argument checks of the setters, before any device work: the sponge
+    (cells within the lattice, a finite non-negative viscosity), the STG / wall
+    parameters (positive length scale and kappa), the inlet profile (every
+    R(y) positive definite, the old profile kept otherwise) and the graph
+    switch."""
+    lib = _abi.lib()
+    rc, h = _create(nx=16, ny=8, nz=4)
+    assert rc == 0
+    dp = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_double))   # noqa: E731
+    E = _abi.LBM_EINVAL
+    assert lib.lbm_set_sponge(h, -1, 0.1) == E
+    assert lib.lbm_set_sponge(h, 17, 0.1) == E
+    assert lib.lbm_set_sponge(h, 4, -0.1) == E
+    assert lib.lbm_set_sponge(h, 4, float("nan")) == E
+    assert lib.lbm_set_sponge(h, 4, 0.1) == 0
+    assert lib.lbm_set_params(h, dp(np.array([0.0, 1.0, 0.4, 7.8]))) == E
+    assert lib.lbm_set_params(h, dp(np.array([0.4, 1.0, -0.4, 7.8]))) == E
+    U, R = np.zeros(8), np.zeros(48)
+    assert lib.lbm_get_inlet_profile(h, dp(U), dp(R)) == 0
+    bad = R.copy()
+    bad[6 * 3 + 1] = -1.0                          # R22 < 0 in row 3
+    assert lib.lbm_set_inlet_profile(h, dp(U), dp(bad)) == E
+    U2, R2 = np.zeros(8), np.zeros(48)
+    lib.lbm_get_inlet_profile(h, dp(U2), dp(R2))
+    assert np.array_equal(U2, U) and np.array_equal(R2, R)      # unchanged
+    assert lib.lbm_set_graphs(None, 1) == E
+    on, n = ct.c_int(), ct.c_long()
+    assert lib.lbm_set_graphs(h, 0) == 0 and lib.lbm_graph_info(h, ct.byref(on), ct.byref(n)) == 0
+    assert on.value == 0 and n.value == 0
+    assert lib.lbm_graph_info(h, None, ct.byref(n)) == E
+    lib.lbm_destroy(h)
