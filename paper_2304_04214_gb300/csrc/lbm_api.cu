@@ -1043,6 +1043,9 @@ int graph_segment(lbm_handle *h) {
     h->prof_count += h->stg_ring;
     h->launches += g->d_launches + 1;            // and the time setter
     h->stg_next_t0 = h->stg_t0 + h->stg_ring;
+    // the graph's wall kernels ran inside it, ordered on the handle's stream
+    // and not on the side stream: a wall-shear reduction follows them there
+    h->fw_side = false;
     ++h->graph_launches;
     return LBM_OK;
 }

@@ -120,3 +120,23 @@ def test_adjoint_windows_between_graph_periods():
     _same(a, b)
     a.close()
     b.close()
+
+
+def test_wall_shear_after_graph_periods():
+    """The asynchronous wall-shear reduction right after steps that ran as a
+    graph reads the forces of the graph's last step: it equals the
+    synchronous reduction and the same call after separate launches."""
+    import torch
+    a, b = _pair("fp32")
+    outs = []
+    for c in (a, b):
+        c.step(192)                       # two periods as graphs in a
+        pinned = torch.empty(2 * c.nx, dtype=torch.float64).pin_memory()
+        c.wall_shear_async(pinned)
+        c.sync()
+        outs.append((pinned.numpy().copy(), c.wall_shear().reshape(-1)))
+    assert a.graph_info()[1] == 2
+    assert np.array_equal(outs[0][0], outs[0][1])
+    assert np.array_equal(outs[0][0], outs[1][0])
+    a.close()
+    b.close()
