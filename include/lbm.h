@@ -129,6 +129,14 @@ int lbm_step(lbm_handle *h, int n);
  * kernel separately (on = 0).  Errors: LBM_EINVAL. */
 int lbm_set_graphs(lbm_handle *h, int on);
 
+/* Failure-detection check: enqueue one block that waits, with the bounded
+ * wait of the staged kernel's copy ring (here 2^14 polls), on a barrier that
+ * nothing completes; it gives up and raises the device timeout flag, so the
+ * next lbm_sync returns LBM_ETIMEOUT (and clears the flag).  Nothing else is
+ * touched.  Errors: LBM_EINVAL, LBM_ESTATE before lbm_bind_memory,
+ * LBM_ECUDA. */
+int lbm_probe_wait_timeout(lbm_handle *h);
+
 /* Whether graphs are on (*on; 0 also after a capture the runtime refused),
  * and how many graph launches lbm_step has made (*launched; each also
  * launches one single-thread kernel that sets the period's start time, which

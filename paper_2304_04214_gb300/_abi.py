@@ -61,6 +61,7 @@ PROTOTYPES = {
     "lbm_set_step_kernel": (ct.c_int, [_h, ct.c_int]),
     "lbm_set_graphs": (ct.c_int, [_h, ct.c_int]),
     "lbm_graph_info": (ct.c_int, [_h, ct.POINTER(ct.c_int), ct.POINTER(ct.c_long)]),
+    "lbm_probe_wait_timeout": (ct.c_int, [_h]),
     "lbm_get_step_kernel": (ct.c_int, [_h, ct.POINTER(ct.c_int)]),
     "lbm_set_sponge": (ct.c_int, [_h, ct.c_int, ct.c_double]),
     "lbm_stats": (ct.c_int, [_h, _dp, _dp, ct.POINTER(ct.c_long)]),

@@ -1216,6 +1216,14 @@ int lbm_set_graphs(lbm_handle *h, int on) {
     return LBM_OK;
 }
 
+int lbm_probe_wait_timeout(lbm_handle *h) {
+    if (!h) return LBM_EINVAL;
+    if (!h->bound) return LBM_ESTATE;
+    lbmk::wait_timeout_probe_kernel<<<1, 32, 0, h->stream>>>(h->d_flags, 1 << 14);
+    h->launches += 1;
+    return cuda_fail(cudaGetLastError());
+}
+
 int lbm_graph_info(const lbm_handle *h, int *on, long *launched) {
     if (!h || !on || !launched) return LBM_EINVAL;
     *on = h->graphs_on ? 1 : 0;

@@ -93,12 +93,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2^22 polls (each poll may itself suspend for a
-// while), so a copy that never lands ends in an error flag, not a hang.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it)
+// Bounded wait: gives up after `polls` polls (~2^22 by default; each poll may
+// itself suspend for a while), so a copy that never lands ends in an error
+// flag, not a hang.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int polls = 1 << 22) {
+    for (int it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// Exercises that path: one block waits, with the same bounded wait, on a
+// barrier that no copy and no thread completes, and raises the timeout flag
+// the way the staged kernel does (read back by lbm_sync as LBM_ETIMEOUT).
+__global__ void wait_timeout_probe_kernel(unsigned *flags, int polls) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(smem_u32(&bar), 0u, polls);
+    if (!ok && threadIdx.x == 0) atomicOr(flags + 2, 1u);
 }
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, int w,
                                             uint32_t bar) {

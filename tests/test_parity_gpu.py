@@ -206,6 +206,24 @@ def test_divergence_is_reported():
     g.sync()              # the flag is cleared once reported
 
 
+def test_device_wait_timeout_is_reported():
+    """Failure detection without a fault: a device wait that nothing completes
+    (the bounded wait of the staged kernel's copy ring) gives up, raises the
+    timeout flag, and lbm_sync reports LBM_ETIMEOUT; the context stays usable
+    and the following steps still match the oracle."""
+    from paper_2304_04214_gb300 import _abi
+    o, g = make_pair(32, 8, 4, n_modes=4, seed=2)
+    assert g.lib.lbm_probe_wait_timeout(g.h) == 0
+    with pytest.raises(_abi.LBMError) as e:
+        g.sync()
+    assert e.value.code == _abi.LBM_ETIMEOUT
+    g.sync()              # cleared once reported
+    o.step(3)
+    g.step(3)
+    er, eu = field_errors(o, g)
+    assert er < 1e-5 and eu < 1e-5
+
+
 def test_async_wall_shear_matches_the_synchronous_call():
     """lbm_wall_shear_async into two pinned buffers in turn gives, step by
     step, what lbm_wall_shear returns; both match the oracle's tau_w."""
