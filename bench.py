@@ -72,10 +72,11 @@ PROF_EVERY = 16
 
 
 def kernel_source_hash():
+    """Hash of the source of the kernels the traffic record holds (the pair,
+    quad and wall-row step kernels, all in lbm_device.cuh)."""
     h = hashlib.sha256()
-    for f in ("lbm_device.cuh", "lbm_staged.cuh"):    # the kernel sources
-        with open(os.path.join(ROOT, "paper_2304_04214_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2304_04214_gb300", "csrc", "lbm_device.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
