@@ -28,6 +28,13 @@
  * return host data synchronize that stream first.  Host pointers are owned
  * by the caller.  Device memory is either bound by the caller
  * (lbm_bind_memory with a pointer) or allocated by the library (pointer NULL).
+ *
+ * Errors common to the calls (each declaration lists only its own):
+ * LBM_EINVAL for a NULL handle or a NULL pointer argument; LBM_ESTATE for a
+ * call that needs device memory before lbm_bind_memory; LBM_ECUDA when a CUDA
+ * runtime call fails (its message is printed to stderr).  Device-side
+ * conditions found while steps run (divergence, a Newton solve that did not
+ * converge, a wait that gave up) are deferred to lbm_sync.
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
@@ -89,7 +96,8 @@ typedef struct {
     void *cuda_stream;        /* cudaStream_t to enqueue on; NULL: default stream */
 } lbm_opts;
 
-/* Fill *opts with the defaults listed above (FP32, stream NULL). */
+/* Fill *opts with the defaults listed above (FP32, stream NULL); NULL is
+ * ignored. */
 void lbm_default_opts(lbm_opts *opts);
 
 /* Create a channel.  Computes the flow constants in FP64 on the host:
@@ -103,7 +111,8 @@ int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg,
                const lbm_opts *opts, lbm_handle **out);
 
 /* Device bytes the handle needs (both lattices, tables, wall and inlet
- * buffers, statistics).  Alignment of the bound pointer: 256 bytes. */
+ * buffers, statistics) into *bytes.  Alignment of the bound pointer: 256
+ * bytes.  No device work; works before lbm_bind_memory. */
 int lbm_required_bytes(const lbm_handle *h, size_t *bytes);
 
 /* Bind device memory: dev_ptr of at least lbm_required_bytes bytes, owned by
@@ -164,7 +173,9 @@ int lbm_sync(lbm_handle *h);
 int lbm_save(lbm_handle *h, const char *path);
 int lbm_load(lbm_handle *h, const char *path);
 
-/* Set the CUDA stream later calls enqueue on (cudaStream_t; NULL = default). */
+/* Set the CUDA stream later calls enqueue on (cudaStream_t; NULL = default).
+ * Work already enqueued stays on the previous stream; the caller orders the
+ * two.  Errors: LBM_EINVAL for a NULL handle. */
 int lbm_set_stream(lbm_handle *h, void *cuda_stream);
 
 /* ---- step kernel variants (all compute the same step of Algorithm 1) ---- */
@@ -186,7 +197,8 @@ int lbm_set_stream(lbm_handle *h, void *cuda_stream);
  * for an unknown kind or a grid the kind does not support. */
 int lbm_set_step_kernel(lbm_handle *h, int kind);
 
-/* The kernel later steps will run (AUTO resolved) into *kind. */
+/* The kernel later steps will run (AUTO resolved) into *kind.  Errors:
+ * LBM_EINVAL for NULL pointers. */
 int lbm_get_step_kernel(const lbm_handle *h, int *kind);
 
 /* Outlet sponge zone (Sec. 4.1 places one before the outlet; its form is not
@@ -204,36 +216,43 @@ int lbm_set_sponge(lbm_handle *h, int cells, double nu_max);
  * sums[(j*nx + i)*7 + c], c = (u, v, w, uu, vv, ww, uv), each summed over z
  * and samples in FP64; utau_sums[w*nx + i] (w = 0 bottom, 1 top) summed over z
  * and samples; *n_samples the number of samples.  Host buffers of nx*ny*7 and
- * 2*nx doubles.  Synchronizes. */
+ * 2*nx doubles.  Synchronizes.  lbm_reset_stats zeroes the accumulators and
+ * the sample count (enqueued, no synchronization).  Errors: the common ones. */
 int lbm_stats(lbm_handle *h, double *sums, double *utau_sums, long *n_samples);
 int lbm_reset_stats(lbm_handle *h);
 
 /* Macroscopic fields of the last collision, eq:density and eq:momentum:
  * rho[c] and u[3*c + a] for cell c = (k*ny + j)*nx + i, host FP64.
  * rho u = sum_q f*_q c_q - F/2 with F the wall force of that collision.
- * Synchronizes. */
+ * Synchronizes.  Errors: the common ones. */
 int lbm_get_fields(lbm_handle *h, double *rho, double *u);
 
 /* Copy the post-collision populations out / in (host FP64, 19*ncell, layout
  * f[q][k][j][i]).  set rounds to the storage type (FP16/BF16 deviations are
- * rounded to nearest after subtracting w_q in FP64). */
+ * rounded to nearest after subtracting w_q in FP64); both synchronize.
+ * Errors: the common ones. */
 int lbm_get_populations(lbm_handle *h, double *f);
 int lbm_set_populations(lbm_handle *h, const double *f);
 
 /* Friction velocity of every wall cell from the last step, host FP64,
- * utau[(w*nz + k)*nx + i] (w = 0 bottom, 1 top).  Synchronizes. */
+ * utau[(w*nz + k)*nx + i] (w = 0 bottom, 1 top).  Synchronizes.  Errors: the
+ * common ones. */
 int lbm_get_utau(lbm_handle *h, double *utau);
 
-/* Time counter t (the STG time of the next step, eq:aux_vec). */
+/* Time counter t (the STG time of the next step, eq:aux_vec); set moves it
+ * (the STG ring is refilled from the new time).  Errors: LBM_EINVAL for
+ * t < 0. */
 int lbm_get_time(const lbm_handle *h, long *t);
 int lbm_set_time(lbm_handle *h, long t);
 
-/* Flow constants: out[0..5] = delta, u_tau,ref, nu, tau0, U_b+, max l_e. */
+/* Flow constants: out[0..5] = delta, u_tau,ref, nu, tau0, U_b+, max l_e
+ * (host values of lbm_create; works before lbm_bind_memory). */
 int lbm_get_constants(const lbm_handle *h, double out[6]);
 
 /* STG inlet velocity u_in(j, k, t) = (U_R(j), 0, 0) + amp a(j) v'(j, k, t)
  * (eq:u_couple, eq:v_fluc, eq:aux_vec) computed by the device kernel for time
- * t; host FP64 out[(k*ny + j)*3 + a].  Synchronizes. */
+ * t; host FP64 out[(k*ny + j)*3 + a].  Synchronizes.  Errors: LBM_EINVAL
+ * for t < 0. */
 int lbm_inlet_velocity(lbm_handle *h, long t, double *out);
 
 /* Inlet mean profile and Reynolds stress, the RANS input of Algorithm 1
@@ -251,7 +270,8 @@ int lbm_set_inlet_profile(lbm_handle *h, const double *U, const double *R);
 int lbm_get_inlet_profile(const lbm_handle *h, double *U, double *R);
 
 /* Wall shear stress tau_w = rho u_tau^2 (Sec. 2.3) of the last step,
- * averaged over z: host out[w*nx + i], w = 0 bottom, 1 top.  Synchronizes. */
+ * averaged over z: host out[w*nx + i], w = 0 bottom, 1 top.  Synchronizes.
+ * Errors: the common ones. */
 int lbm_wall_shear(lbm_handle *h, double *out);
 
 /* The same reduction enqueued without synchronizing: out (2*nx doubles,
@@ -325,7 +345,8 @@ typedef struct {
  * checkpoint every `ckpt_every` steps (window a multiple of ckpt_every):
  * window/ckpt_every checkpoint lattices, ckpt_every - 1 recomputed lattices, two
  * adjoint lattices, u_tau of every step, the STG field and the inlet adjoint of
- * every step. */
+ * every step.  No device work.  Errors: LBM_EINVAL for window < 1,
+ * ckpt_every < 1 or window not a multiple of ckpt_every. */
 int lbm_adjoint_required_bytes(const lbm_handle *h, int window, int ckpt_every, size_t *bytes);
 
 /* Bind the adjoint workspace (caller-owned, 256-byte aligned, at least
@@ -338,26 +359,34 @@ int lbm_adjoint_bind(lbm_handle *h, int window, int ckpt_every, void *dev_ptr, s
  * s_0 and every ckpt_every-th state, then for each segment in reverse
  * recompute its states from the checkpoint and run the adjoint steps
  * backwards.  *J and dJ_dtheta[4] are host FP64.  dJ/ds_0 is kept for
- * lbm_adjoint_state_gradient.  Synchronizes. */
+ * lbm_adjoint_state_gradient.  Synchronizes.  Errors: LBM_EINVAL for a
+ * window or objective range the workspace or the grid does not fit, the
+ * common ones otherwise (binds a workspace first if none is bound). */
 int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_objective *obj, double *J,
                      double dJ_dtheta[4]);
 
-/* dJ/ds_0 of the last lbm_adjoint_step, host FP64 [19][ncell]. */
+/* dJ/ds_0 of the last lbm_adjoint_step, host FP64 [19][ncell].
+ * Errors: LBM_ESTATE before a completed lbm_adjoint_step. */
 int lbm_adjoint_state_gradient(lbm_handle *h, double *lambda0);
 
 /* One vector-Jacobian product of the time step at the current state (which
  * is left unchanged): given lambda_next = a row vector on s_{t+1} (host FP64
  * [19][ncell]) return lambda_prev = lambda_next ds_{t+1}/ds_t and
- * dtheta = lambda_next ds_{t+1}/dtheta.  Needs an adjoint workspace. */
+ * dtheta = lambda_next ds_{t+1}/dtheta.  Needs an adjoint workspace
+ * (lbm_adjoint_bind).  Errors: the common ones (LBM_ESTATE without one). */
 int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, double dtheta[4]);
 
 /* Replace the model parameters theta = (ell_e, amp, kappa, B) and rebuild
- * the tables that depend on them (the flow constants of lbm_create stay). */
+ * the tables that depend on them (the flow constants of lbm_create stay);
+ * synchronizes after the upload.  Errors: LBM_EINVAL for ell_e <= 0 or
+ * kappa <= 0. */
 int lbm_set_params(lbm_handle *h, const double theta[4]);
 
+/* Free the handle, after the work it enqueued has finished; device memory is
+ * freed only if the library allocated it.  NULL is ignored. */
 void lbm_destroy(lbm_handle *h);
 
-/* Static string for an error code. */
+/* Static string for an error code (a generic text for unknown codes). */
 const char *lbm_error_string(int code);
 
 #ifdef __cplusplus
