@@ -1,17 +1,23 @@
 """Benchmark of the fused D3Q19 MRT-LES + STG channel step on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                [--config c2] [--precision fp32|fp16|bf16]
+                [--config c4] [--precision fp32|fp16|bf16]
 
 One bench step is one time step of the method over the whole lattice: the STG
-inlet kernel and the fused stream/inlet/wall/collide kernel, with the FP64
-statistics accumulated every 10 steps.  Default workload: the Re_tau = 1000
-channel, 384 x 96 x 96 lattice, N = 200 STG modes, FP32 storage.  The two
-lattices (538 MB) exceed the 129 MB L2, so no L2 flush is needed between steps.
+inlet ring refill (every 64 steps, beside the steps), the interior and wall-row
+step kernels (stream, inlet, wall model, collide), and the FP64 statistics
+every 10 steps.  Default workload: the Re_tau = 5200 channel, 1536 x 192 x 384
+lattice (113 M cells), N = 400 STG modes, FP32 storage; the two lattices
+(17.2 GB) exceed the 129 MB L2, so no L2 flush is needed between steps.  The
+headline is the median of repeated regions of exactly K steps; the step
+kernels' roofline comes from a separate pass; the line also carries the 16-bit
+storages and the FP16 / FP32 ratios at three lattice sizes, the adjoint cost,
+an end-to-end loop through the C ABI with host buffers, and the FP64 oracle on
+the host cores.
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances its
-own independent channel (an ensemble member with its own STG draws): weak
-scaling, no collective on the data path.
+Prints one JSON line (rank 0).  With N > 1 (torchrun) the channel is cut into
+N x-slabs, one per GPU, with the halo moved over NCCL before every step:
+strong scaling, the whole channel's cells per second.
 """
 import argparse
 import ctypes as ct
@@ -66,9 +72,6 @@ def measured_peaks():
             return json.load(fh), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
-
-
-PROF_EVERY = 16
 
 
 def kernel_source_hash():
@@ -227,6 +230,93 @@ def run_reference(args, cfg, ws, rank):
 
 
 # --------------------------------------------------------------------------
+def timed_region(ch, steps, barrier, stream):
+    """Device time in ms of exactly `steps` steps (of a channel, or of this
+    rank's slab with its halo exchanges): barrier and synchronize on both
+    sides, CUDA events on the library's stream."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    ch.step(steps)
+    e1.record(stream)
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def repeat_count(first_ms, min_total_ms=1000.0, lo=3, hi=50):
+    """Repeats of the timed region: at least `lo`, and enough that all of them
+    together last about `min_total_ms`."""
+    return int(max(lo, min(hi, -(-min_total_ms // max(first_ms, 1e-3)))))
+
+
+def median(xs):
+    s = sorted(xs)
+    n = len(s)
+    return s[n // 2] if n % 2 else 0.5 * (s[n // 2 - 1] + s[n // 2])
+
+
+def kernel_pass(ch, steps, stepper=None):
+    """Mean CUDA-event time in ms of one step's step kernels (interior and wall
+    rows, the side stream joined inside), every step bracketed, graphs off:
+    a pass of its own, after the headline region, so that its events do not
+    cost the timed steps anything.  `stepper` (a slab) steps with its halo
+    exchanges, which stay outside the brackets."""
+    import ctypes as ct
+    from paper_2304_04214_gb300 import _abi
+    lib, h = ch.lib, ch.h
+    ms_k, nk, nall = ct.c_double(), ct.c_long(), ct.c_long()
+    ch.set_graphs(False)
+    _abi.check(lib.lbm_profile_enable(h, 1), "lbm_profile_enable")
+    lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))    # reset
+    (stepper or ch).step(steps)
+    _abi.check(lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall)), "lbm_profile_read")
+    lib.lbm_profile_enable(h, 0)
+    ch.set_graphs(True)
+    return ms_k.value / max(nk.value, 1), nk.value
+
+
+def storage_sweep(dev, args, barrier, stream, fp32_c4_mlups):
+    """Whole-step MLUPS of the other storages and lattices, each the median of
+    three timed regions of about 0.3 s: the 16-bit storages at 1536x192x384
+    and FP32 / FP16 at 768x128x192 and 384x96x96, with the FP16 / FP32
+    ratios the 1.6x target refers to."""
+    import torch
+    from paper_2304_04214_gb300.channel import LBMChannel
+    peaks, _ = measured_peaks()
+    out = {}
+    for key, prec in (("c4", "fp16"), ("c4", "bf16"), ("c3", "fp32"), ("c3", "fp16"),
+                      ("c2", "fp32"), ("c2", "fp16")):
+        if key == args.config and prec == args.precision:
+            continue
+        cfg = CONFIGS[key]
+        nx, ny, nz = cfg["shape"]
+        ncell = nx * ny * nz
+        ch = LBMChannel(nx, ny, nz, re_tau=cfg["re_tau"], n_modes=cfg["n_modes"], seed=cfg["seed"],
+                        precision=prec, stats_every=STATS_EVERY, device=dev)
+        ch.step(20)
+        first = timed_region(ch, 64, barrier, stream)
+        steps = max(64, int(300.0 / max(first / 64, 1e-4)))
+        ms = median([timed_region(ch, steps, barrier, stream) for _ in range(3)])
+        kern_ms, _ = kernel_pass(ch, 64)
+        ch.close()
+        del ch
+        torch.cuda.empty_cache()
+        mlups = ncell * steps / (ms * 1e-3) / 1e6
+        b = BYTES_PER_CELL[prec] * ncell
+        out[f"{key}_{prec}"] = {"lattice": [nx, ny, nz], "mlups": round(mlups, 1), "steps": steps,
+                                "ms_per_step": round(ms / steps, 5), "kernel_ms": round(kern_ms, 5),
+                                "frac_whole_step": round(b / (ms / steps * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                                "frac": round(b / (kern_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+    m = {k: v["mlups"] for k, v in out.items()}
+    if args.config == "c4" and args.precision == "fp32":
+        m["c4_fp32"] = fp32_c4_mlups
+    ratios = {c: round(m[f"{c}_fp16"] / m[f"{c}_fp32"], 3) for c in ("c2", "c3", "c4")
+              if f"{c}_fp16" in m and f"{c}_fp32" in m}
+    return out, ratios
+
+
 def run_native(args, cfg, ws, rank, local):
     import numpy as np
     import torch
@@ -240,10 +330,17 @@ def run_native(args, cfg, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     nx, ny, nz = cfg["shape"]
     ncell = nx * ny * nz
-    ch = LBMChannel(nx, ny, nz, re_tau=cfg["re_tau"], n_modes=cfg["n_modes"],
-                    seed=cfg["seed"] + 1000 * rank, precision=args.precision,
-                    stats_every=STATS_EVERY, step_kernel=args.kernel, device=dev)
+    kw = dict(re_tau=cfg["re_tau"], n_modes=cfg["n_modes"], seed=cfg["seed"], precision=args.precision,
+              stats_every=STATS_EVERY, step_kernel=args.kernel, device=dev)
+    if ws > 1:
+        # one channel cut into x-slabs, one per rank, halos over NCCL: strong scaling
+        from paper_2304_04214_gb300.slab import P2PTransport, SlabChannel
+        run = SlabChannel(nx, ny, nz, rank, ws, P2PTransport(device_buffers=True), **kw)
+        ch = run.ch
+    else:
+        run = ch = LBMChannel(nx, ny, nz, **kw)
     ch.set_graphs(args.graphs == "on")
+    local_cells = ch.ncell
     lib, h = ch.lib, ch.h
     kernel = ch.step_kernel
     stream = torch.cuda.current_stream(dev)
@@ -254,39 +351,40 @@ def run_native(args, cfg, ws, rank, local):
             torch.distributed.barrier()
 
     # ---- warm-up ----
-    ch.step(args.warmup)
+    run.step(args.warmup)
     ch.sync()
     barrier()
 
-    # ---- timed region: K steps, device events, kernel events, clocks ----
-    # events on the library's stream bracket each graph launch (64 steps) and
-    # the kernels of every timed_every-th separately launched step (an event
-    # pair costs the stream a few us, so timing every step would inflate the
-    # step it measures)
-    _abi.check(lib.lbm_profile_enable(h, args.timed_every), "lbm_profile_enable")
+    # ---- timed region: exactly K steps, repeated (median), nothing else on
+    # the stream; clocks sampled throughout ----
     ms_k, nk, nall = ct.c_double(), ct.c_long(), ct.c_long()
-    lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))   # reset counters
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    regions = []
     with ClockSampler(smi_index(local)) as clk:
-        barrier()
-        e0.record(stream)
-        ch.step(args.steps)
-        e1.record(stream)
-        barrier()
-    ms = e0.elapsed_time(e1)
-    lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))
-    lib.lbm_profile_enable(h, 0)
+        lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))   # reset the launch count
+        regions.append(timed_region(run, args.steps, barrier, stream))
+        lib.lbm_profile_read(h, ct.byref(ms_k), ct.byref(nk), ct.byref(nall))
+        launches = int(nall.value)
+        reps = repeat_count(regions[0]) if args.repeats <= 0 else args.repeats
+        if ws > 1:                                   # every rank times the same number of regions
+            reps = int(max_over_ranks(reps, ws, dev))
+        for _ in range(reps - 1):
+            regions.append(timed_region(run, args.steps, barrier, stream))
     ch.sync()
+    ms = median(regions)
     ms = max_over_ranks(ms, ws, dev)
-    value = ncell * ws * args.steps / (ms * 1e-3) / 1e6
+    value = ncell * args.steps / (ms * 1e-3) / 1e6      # the whole channel, over all ranks
+    ms_step = ms / args.steps
 
-    # ---- roofline of the fused step kernel ----
+    # ---- roofline of the step kernels, from a pass of its own ----
     peaks, peak_kind = measured_peaks()
-    kern_ms = ms_k.value / max(nk.value, 1)
-    alg_bytes = BYTES_PER_CELL[args.precision] * ncell
+    kern_steps = max(64, min(args.steps, 256))
+    kern_ms, kern_n = kernel_pass(ch, kern_steps, run if ws > 1 else None)
+    alg_bytes = BYTES_PER_CELL[args.precision] * local_cells          # this GPU's lattice
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     traffic = recorded_traffic(args.config, args.precision, kernel, ncell)
+    if kern_ms > ms_step:
+        print(f"bench: step kernels {kern_ms:.5f} ms > whole step {ms_step:.5f} ms", file=sys.stderr)
+    traffic = traffic if ws == 1 else None
 
     # ---- end to end through the C ABI with host buffers ----
     # each step: the RANS-side inlet profile (U, R) from pinned host memory,
@@ -299,12 +397,15 @@ def run_native(args, cfg, ws, rank, local):
     evs = [torch.cuda.Event() for _ in range(2)]
     dp = lambda x: ct.cast(x.data_ptr(), ct.POINTER(ct.c_double))   # noqa: E731
     _abi.check(lib.lbm_get_inlet_profile(h, dp(U), dp(R)), "lbm_get_inlet_profile")
-    n_e2e = max(3, min(args.steps, 2000))
+    n_e2e = int(max(args.steps, min(2000, 500.0 / max(ms_step, 1e-4))))
     taken = []
 
     def coupled_step(n):
         _abi.check(lib.lbm_set_inlet_profile(h, dp(U), dp(R)), "lbm_set_inlet_profile")
-        _abi.check(lib.lbm_step(h, 1), "lbm_step")
+        if ws > 1:
+            run.step(1)
+        else:
+            _abi.check(lib.lbm_step(h, 1), "lbm_step")
         _abi.check(lib.lbm_wall_shear_async(h, dp(tws[n % 2])), "lbm_wall_shear_async")
         evs[n % 2].record(stream)
         if n >= 1:                                 # step n - 1's wall shear is on the host
@@ -323,9 +424,16 @@ def run_native(args, cfg, ws, rank, local):
     barrier()
     dt_e2e = time.perf_counter() - t0
     dt_e2e = max_over_ranks(dt_e2e, ws, dev)
-    e2e = ncell * ws * n_e2e / dt_e2e / 1e6
+    e2e = ncell * n_e2e / dt_e2e / 1e6
     assert len(taken) == n_e2e and np.all(np.isfinite(taken)) and np.all(np.isfinite(tws[0].numpy()))
     ch.sync()
+    run.close()
+    del ch, run
+    torch.cuda.empty_cache()
+
+    sweep, ratios = None, None
+    if rank == 0 and ws == 1 and not args.no_sweep:
+        sweep, ratios = storage_sweep(dev, args, barrier, stream, value)
 
     adjoint = None
     if rank == 0 and not args.no_adjoint:
@@ -335,42 +443,52 @@ def run_native(args, cfg, ws, rank, local):
     if rank == 0:
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
-            m, thr, sample, _, _ = cpu_oracle_mlups(cfg, budget_s=10.0)
+            # a spanwise slice of the lattice keeps the oracle's memory (360 B
+            # per cell) and the sample's duration bounded
+            nzs = max(1, min(nz, int(2.0e6 // (nx * ny))))
+            m, thr, sample, _, _ = cpu_oracle_mlups(cfg, budget_s=10.0, nz_sample=nzs)
             cpu = {"value": round(m, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
                    "sample": sample}
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "repeats": len(regions), "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
+            "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["name"] + f", {args.precision.upper()} storage",
                        "lattice": list(cfg["shape"]), "re_tau": cfg["re_tau"],
                        "n_modes": cfg["n_modes"], "storage": args.precision,
                        "stats_every": STATS_EVERY,
                        "l2": "no flush: the two lattices (%.0f MB) exceed the 129 MB L2"
-                             % (2 * BYTES_PER_CELL[args.precision] / 2 * ncell / 1e6),
-                       "parallelism": "replicas" if ws > 1 else "single",
+                             % (BYTES_PER_CELL[args.precision] * local_cells / 1e6),
+                       "timing": "median of %d regions of exactly %d steps, each bracketed by a barrier and a "
+                                 "device synchronize, CUDA events on the library's stream"
+                                 % (len(regions), args.steps),
+                       "parallelism": f"x-slabs over {ws} GPUs, halo over NCCL" if ws > 1 else "single",
                        "cuda_graphs": args.graphs == "on"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(achieved / peaks["hbm_gbs"], 4),
                          "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": KERNEL_NAMES[kernel] + (
-                             " (64-step CUDA graphs: the step kernels with the statistics and the"
-                             " ring refill, per step)" if args.graphs == "on" else ""),
-                         "kernel_ms": round(kern_ms, 5),
-                         "timed_steps": nk.value, "timed_every": args.timed_every,
+                         "kernel": KERNEL_NAMES[kernel],
+                         "kernel_ms": round(kern_ms, 5), "kernel_timed_steps": kern_n,
+                         "kernel_timing": "separate pass after the timed region, graphs off, every step's "
+                                          "step kernels bracketed by CUDA events",
+                         "kernel_ms_le_step_ms": bool(kern_ms <= ms_step),
+                         "frac_whole_step": round(alg_bytes / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
                          "algorithmic_bytes": alg_bytes},
             "cpu_baseline": cpu,
-            "e2e": {"value": round(e2e, 1), "unit": "MLUPS",
+            "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "steps": n_e2e,
                     "h2d_bytes_per_step": 7 * ny * 4, "d2h_bytes_per_step": 2 * nx * 8},
-            "gpu_launches": int(nall.value),
+            "gpu_launches": launches,
             "clocks": clk.summary(),
+            "storages": sweep,
+            "fp16_over_fp32": ratios,
             "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
-    ch.close()
     if ws > 1:
+        torch.distributed.barrier()               # rank 0's extra work (adjoint, line) is done
         torch.distributed.destroy_process_group()
     return line
 
@@ -412,18 +530,20 @@ def adjoint_timing(dev, reps=3):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="c4", choices=sorted(CONFIGS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "quad", "staged"])
     ap.add_argument("--graphs", default="on", choices=["on", "off"],
                     help="launch STG ring periods of steps as CUDA graphs")
-    ap.add_argument("--timed-every", type=int, default=PROF_EVERY,
-                    help="bracket the step kernels of every n-th step with CUDA events")
+    ap.add_argument("--repeats", type=int, default=0,
+                    help="timed regions of K steps (median reported); 0: enough for about 1 s, at least 3")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the other storages and lattices (16-bit / FP32 ratios)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -28,6 +28,11 @@
  * return host data synchronize that stream first.  Host pointers are owned
  * by the caller.  Device memory is either bound by the caller
  * (lbm_bind_memory with a pointer) or allocated by the library (pointer NULL).
+ * A handle belongs to one CUDA device, the device of its memory: while a call
+ * runs, that device is current (the caller's current device is put back
+ * before the call returns), so a handle may be used from any current device;
+ * its stream (lbm_opts.cuda_stream, lbm_set_stream) must belong to that
+ * device.
  *
  * Errors common to the calls (each declaration lists only its own):
  * LBM_EINVAL for a NULL handle or a NULL pointer argument; LBM_ESTATE for a
@@ -117,16 +122,24 @@ int lbm_required_bytes(const lbm_handle *h, size_t *bytes);
 
 /* Bind device memory: dev_ptr of at least lbm_required_bytes bytes, owned by
  * the caller (the library never frees it); or dev_ptr NULL to let the library
- * cudaMalloc it (freed by lbm_destroy).  Uploads the tables and initializes
- * the lattice to f^eq(1, (U_R(y), 0, 0)) with U_R the inlet mean profile.
- * Errors: LBM_ENOMEM if bytes is too small, LBM_EINVAL if misaligned,
- * LBM_ESTATE if already bound, LBM_ECUDA. */
+ * cudaMalloc it on the current device (freed by lbm_destroy).  The device of
+ * that memory becomes the handle's device.  Uploads the tables and
+ * initializes the lattice to f^eq(1, (U_R(y), 0, 0)) with U_R the inlet mean
+ * profile.  Errors: LBM_ENOMEM if bytes is too small, LBM_EINVAL if
+ * misaligned or not device memory, LBM_ESTATE if already bound, LBM_ECUDA. */
 int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes);
 
 /* Enqueue n time steps of Algorithm 1 on the handle's stream and return
- * without synchronizing.  Each step: inlet velocity (steps 4-5), then one
- * fused kernel doing pull streaming with the boundary rules, the regularized
- * inlet (steps 6-8), the wall model (steps 9-14) and the collision (step 15).
+ * without synchronizing.  Each step: the inlet velocity of steps 4-5 comes
+ * from a ring of STG time levels filled ahead of the steps (on a second
+ * stream of the handle); then two kernels read the previous state and write
+ * disjoint rows of the next one: the interior kernel (rows 1..ny-2, on the
+ * handle's stream) does pull streaming with the boundary rules, the
+ * regularized inlet (steps 6-8) and the collision (step 15); the wall-row
+ * kernel (rows 0 and ny-1, on a side stream forked from and joined back into
+ * the handle's stream) does the same for the first off-wall cells with the
+ * wall model (steps 9-14).  (Odd nx, or LBM_KERNEL_CELL: one kernel for all
+ * rows.)
  * With CUDA graphs on (the default, lbm_set_graphs), whole periods of the STG
  * ring (64 steps where the inlet plane allows) that fit in n are launched as
  * one graph each, built the first time a period's launch state occurs; the
@@ -166,7 +179,9 @@ int lbm_sync(lbm_handle *h);
  * synchronizes the stream.  lbm_load restores a handle created with the same
  * grid, storage, Re_tau, options and STG draws: the next steps are
  * bit-identical to those of the run that saved.  It reads and checks the
- * whole file before it changes the handle.  Errors: LBM_ESTATE before
+ * whole file before it changes the handle, then waits for all work the handle
+ * has enqueued (on any of its streams) before it replaces the state, so it
+ * may follow lbm_step without a synchronization.  Errors: LBM_ESTATE before
  * lbm_bind_memory; LBM_EINVAL for a file that cannot be opened, read or
  * written, a foreign or corrupted file (magic, version, sizes, checksum), or
  * one saved by a channel created differently; LBM_ECUDA. */
@@ -211,6 +226,45 @@ int lbm_get_step_kernel(const lbm_handle *h, int *kind);
  * files.  Errors: LBM_EINVAL for cells outside [0, nx] or nu_max negative or
  * not finite. */
 int lbm_set_sponge(lbm_handle *h, int cells, double nu_max);
+
+/* ---- x-slab domain decomposition (one handle per rank; no counterpart in
+ * the paper, whose Algorithm 1 runs the cell loop over one domain) ----
+ *
+ * A channel of nx_global cells along x is cut into slabs of consecutive x
+ * columns, one handle each.  A handle is created with its local lattice:
+ * its owned columns plus ghost columns on each side that has a neighbouring
+ * slab (the inlet and outlet stay the global faces: the first slab starts with
+ * the inlet column, the last ends with the outlet column).  Before every step,
+ * the innermost ghost column on each side must hold the neighbour's
+ * post-collision populations that stream into this slab: the five with
+ * c_x = +1 on the left, the five with c_x = -1 on the right (every other
+ * population of a ghost column is never read by an owned cell).  The kernels
+ * step ghost columns like any cell of the lattice ends (left: inlet, right:
+ * zero-gradient outlet); their results are not used.  With the halo moved
+ * exactly, the owned columns are bit for bit those of the undivided channel.
+ *
+ * lbm_set_slab: local column c is global column c + x_offset; this handle owns
+ * local columns [own_lo, own_hi).  Call before lbm_set_sponge (whose zone is
+ * in global columns).  Errors: LBM_EINVAL for a range outside the lattice, or
+ * a slab whose lattice ends are not the global faces where it holds them.
+ *
+ * lbm_halo_bytes: bytes of one face's halo buffer, 5 x ny x nz stored words
+ * (FP32: 4 bytes, 16-bit storage: 2 bytes), layout [5][nz][ny].
+ *
+ * lbm_halo_pack (enqueued): copy the populations this slab sends across
+ * `face` (LBM_FACE_LEFT: the c_x = -1 populations of its first owned column;
+ * LBM_FACE_RIGHT: the c_x = +1 populations of its last owned column) into the
+ * caller's device buffer.  lbm_halo_unpack (enqueued): copy a neighbour's
+ * buffer into the ghost column next to the owned range on `face`.  Moving the
+ * buffers between ranks (NCCL, a peer copy, host staging) is the caller's.
+ * Errors: LBM_EINVAL for a bad face, or a face with no ghost column
+ * (unpack) or no neighbour to send to; LBM_ESTATE before lbm_bind_memory. */
+#define LBM_FACE_LEFT  0
+#define LBM_FACE_RIGHT 1
+int lbm_set_slab(lbm_handle *h, int nx_global, int x_offset, int own_lo, int own_hi);
+int lbm_halo_bytes(const lbm_handle *h, size_t *bytes);
+int lbm_halo_pack(lbm_handle *h, int face, void *dev_buf);
+int lbm_halo_unpack(lbm_handle *h, int face, const void *dev_buf);
 
 /* Statistics accumulated every stats_every steps since the last reset:
  * sums[(j*nx + i)*7 + c], c = (u, v, w, uu, vv, ww, uv), each summed over z
@@ -300,9 +354,9 @@ int lbm_wall_shear_async(lbm_handle *h, double *out);
  * synchronize the device or fail under memory pressure.  Every GPU that loads
  * the library holds the 512 KiB until the process exits.
  *
- * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps the
+ * The first call for a handle on a given device looks the array's address on
+ * that device up (cudaGetSymbolAddress, with the handle's device current);
+ * make that first call before any stream capture.  All calls share the one array and it keeps the
  * last call's contents; each call overwrites the 2*nx entries it uses before
  * reading them, and copies them to `out` before it returns.  Two calls whose
  * GPU work overlaps (different streams with no ordering between them) race on
@@ -310,6 +364,20 @@ int lbm_wall_shear_async(lbm_handle *h, double *out);
  * LBM_EINVAL, LBM_ESTATE, LBM_ECUDA as for lbm_wall_shear. */
 #define LBM_NOALLOC_MAX_NX 32768
 int lbm_wall_shear_noalloc(lbm_handle *h, double *out);
+
+/* Debugging aid: guard bands (a stand-in for a memory checker, which is not
+ * available everywhere).  lbm_debug_guard_bands, before lbm_bind_memory, puts
+ * a band of at least `bytes` bytes before the first buffer of the device
+ * arena and right after the end of every buffer (and likewise in the adjoint
+ * workspace), filled with the byte 0xA5; lbm_required_bytes and
+ * lbm_adjoint_required_bytes count them.  bytes = 0 (the default): none.
+ * lbm_debug_check_guards waits for all work of the handle and sets *changed
+ * to the number of band bytes that no longer hold the pattern: a write past
+ * the end (or before the start) of a buffer shows there.  Errors:
+ * LBM_EINVAL for bytes < 0; LBM_ESTATE for guard bands after
+ * lbm_bind_memory or a check before it. */
+int lbm_debug_guard_bands(lbm_handle *h, int bytes);
+int lbm_debug_check_guards(lbm_handle *h, long long *changed);
 
 /* Instrumentation.  While enabled (on > 0), every on-th separately launched
  * step (interior and wall-row kernels, from the first one after the call) is

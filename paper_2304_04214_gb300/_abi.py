@@ -14,6 +14,7 @@ KERNELS = {"auto": LBM_KERNEL_AUTO, "cell": LBM_KERNEL_CELL, "pair": LBM_KERNEL_
            "staged": LBM_KERNEL_STAGED, "quad": LBM_KERNEL_QUAD}
 LBM_NOALLOC_MAX_NX = 32768
 LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2
+LBM_FACE_LEFT, LBM_FACE_RIGHT = 0, 1
 PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16_DEV, "bf16": LBM_BF16_DEV}
 
 
@@ -80,6 +81,12 @@ PROTOTYPES = {
     "lbm_wall_shear": (ct.c_int, [_h, _dp]),
     "lbm_wall_shear_async": (ct.c_int, [_h, _dp]),
     "lbm_wall_shear_noalloc": (ct.c_int, [_h, _dp]),
+    "lbm_set_slab": (ct.c_int, [_h, ct.c_int, ct.c_int, ct.c_int, ct.c_int]),
+    "lbm_halo_bytes": (ct.c_int, [_h, ct.POINTER(ct.c_size_t)]),
+    "lbm_halo_pack": (ct.c_int, [_h, ct.c_int, ct.c_void_p]),
+    "lbm_halo_unpack": (ct.c_int, [_h, ct.c_int, ct.c_void_p]),
+    "lbm_debug_guard_bands": (ct.c_int, [_h, ct.c_int]),
+    "lbm_debug_check_guards": (ct.c_int, [_h, ct.POINTER(ct.c_longlong)]),
     "lbm_profile_enable": (ct.c_int, [_h, ct.c_int]),
     "lbm_profile_read": (ct.c_int, [_h, _dp, ct.POINTER(ct.c_long), ct.POINTER(ct.c_long)]),
     "lbm_adjoint_required_bytes": (ct.c_int, [_h, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]),

@@ -107,8 +107,68 @@ def run_paper_case(re_tau, lbu, n_modes=100, seed=1, precision="fp32", stats_eve
     return res
 
 
+STORAGE_CASES = {
+    "c2": dict(shape=(384, 96, 96), re_tau=1000.0, n_modes=200, seed=2),
+    "c3": dict(shape=(768, 128, 192), re_tau=2000.0, n_modes=300, seed=3),
+}
+
+
+def storage_report(case, avg_steps=20000, spin_through=2.0, twins=2, stats_every=1):
+    """Long-run profiles of one channel in FP32, FP16 and BF16 storage, and of
+    FP32 runs started 1e-6 apart (`twins`, the sampling spread of the average):
+    spin-up of spin_through domain-through times, then statistics every
+    stats_every steps for avg_steps steps; profiles U, <u'u'>, <v'v'>, <w'w'>,
+    <u'v'> averaged over z, the samples and x >= nx/4.  Errors: max over y of
+    |difference| / max over y of |FP32 profile|, against the FP32 run; and the
+    pointwise difference of the final streamwise velocity (how far the runs
+    have decorrelated)."""
+    import torch
+    from .channel import LBMChannel
+    from .inputs import noise
+    cfg = STORAGE_CASES[case]
+    nx, ny, nz = cfg["shape"]
+    spin = int(round(spin_through * nx / 0.05))
+    names = ("U", "uu", "vv", "ww", "uv")
+
+    def run(precision, perturb=None):
+        ch = LBMChannel(nx, ny, nz, re_tau=cfg["re_tau"], n_modes=cfg["n_modes"], seed=cfg["seed"],
+                        precision=precision, stats_every=stats_every)
+        if perturb is not None:
+            f = ch.populations()
+            ch.set_populations(f * (1.0 + 1e-6 * noise(f.shape, seed=perturb)))
+        ch.step(spin)
+        ch.reset_stats()
+        ch.step(avg_steps)
+        s, ut, n = ch.stats()
+        _, u = ch.fields()
+        ch.close()
+        torch.cuda.empty_cache()
+        p = profiles(s, ut, n, nz)
+        x0 = nx // 4
+        prof = [p[k][:, x0:].mean(axis=1) for k in names]
+        return prof, u[..., 0]
+
+    ref, u_ref = run("fp32")
+
+    def errs(prof, u):
+        e = {k: float(np.max(np.abs(b - a)) / np.max(np.abs(a))) for k, a, b in zip(names, ref, prof)}
+        e["pointwise_u"] = float(np.max(np.abs(u - u_ref)) / np.max(np.abs(u_ref)))
+        return e
+
+    out = dict(case=case, lattice=[nx, ny, nz], re_tau=cfg["re_tau"], n_modes=cfg["n_modes"],
+               spin_steps=spin, avg_steps=avg_steps, stats_every=stats_every,
+               profile_max={k: float(np.max(np.abs(a))) for k, a in zip(names, ref)})
+    for prec in ("fp16", "bf16"):
+        out[prec] = errs(*run(prec))
+    out["fp32_twins"] = [errs(*run("fp32", perturb=300 + t)) for t in range(twins)]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--storage-report", choices=sorted(STORAGE_CASES),
+                    help="long-run FP16 / BF16 profile errors against FP32 on a bench lattice")
+    ap.add_argument("--avg-steps", type=int, default=20000)
     ap.add_argument("--re-tau", type=float, default=1000.0)
     ap.add_argument("--lbu", type=int, default=40, help="cells across the channel height H")
     ap.add_argument("--modes", type=int, default=100)
@@ -118,6 +178,9 @@ def main():
     ap.add_argument("--sponge", type=float, default=0.0, help="outlet sponge thickness in delta (0: none)")
     ap.add_argument("--sponge-nu", type=float, default=0.1, help="viscosity added at the sponge's end")
     a = ap.parse_args()
+    if a.storage_report:
+        print(json.dumps(storage_report(a.storage_report, avg_steps=a.avg_steps)), flush=True)
+        return
     print(json.dumps(run_paper_case(a.re_tau, a.lbu, n_modes=a.modes, precision=a.precision,
                                     through=a.through, start=a.start, sponge_delta=a.sponge,
                                     sponge_nu=a.sponge_nu)), flush=True)

@@ -29,7 +29,7 @@ class LBMChannel:
     def __init__(self, nx, ny, nz, re_tau=1000.0, n_modes=100, uniforms=None, seed=1,
                  precision="fp32", u_bulk=0.05, c_smag=0.01, kappa=0.4, B=7.8, ell_e=0.4,
                  amp=1.0, k_ratio=1.01, beta_kmin=0.5, wall_model=True, inlet=True,
-                 stats_every=0, step_kernel="auto", stream=None, device=None):
+                 stats_every=0, step_kernel="auto", stream=None, device=None, guard_bytes=0):
         import torch
         self._torch = torch
         self.lib = _abi.lib()
@@ -58,6 +58,8 @@ class LBMChannel:
         _abi.check(self.lib.lbm_create(ct.byref(grid), float(re_tau), ct.byref(stg), ct.byref(opts),
                                        ct.byref(h)), "lbm_create")
         self.h = h
+        if guard_bytes:
+            _abi.check(self.lib.lbm_debug_guard_bands(self.h, int(guard_bytes)), "lbm_debug_guard_bands")
         nbytes = ct.c_size_t()
         _abi.check(self.lib.lbm_required_bytes(self.h, ct.byref(nbytes)), "lbm_required_bytes")
         self.nbytes = nbytes.value
@@ -138,6 +140,13 @@ class LBMChannel:
     def load(self, path):
         """Restore a state written by save() from a channel created alike."""
         _abi.check(self.lib.lbm_load(self.h, str(path).encode()), "lbm_load")
+
+    def guard_bytes_changed(self):
+        """Bytes of the guard bands (guard_bytes > 0 at creation) that no longer
+        hold their fill pattern."""
+        n = ct.c_longlong()
+        _abi.check(self.lib.lbm_debug_check_guards(self.h, ct.byref(n)), "lbm_debug_check_guards")
+        return n.value
 
     # ---- host copies ----
     def fields(self):

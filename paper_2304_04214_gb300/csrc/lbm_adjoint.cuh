@@ -549,6 +549,228 @@ __global__ void __launch_bounds__(128, LBM_ADJ_MINB) adjoint_kernel(const __grid
 }
 
 // ---------------------------------------------------------------------------
+// Interior rows, two x-adjacent cells (i0, i0 + 1) per thread with packed FP32x2
+// arithmetic -- the reverse of collide_pairs2<false, false> and of the pull,
+// the same chain as adjoint_cell written for two cells at once.  Only regular
+// pairs take this path: a pair holding the inlet cell, or a cell whose
+// populations the outlet's clamped pull reads twice, goes through
+// adjoint_cell one cell at a time.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ V2 vsel(bool a, bool b, V2 v) {   // per-lane keep or zero
+    return make_float2(a ? v.x : 0.0f, b ? v.y : 0.0f);
+}
+
+// Reverse of the force-free collision of two cells.  lam: dJ/df* of the two
+// cells; (lux, luy): direct dJ/du seeds.  Returns the adjoint of the pulled
+// populations in lp (the identity part lam included).
+__device__ __forceinline__ void collide_adjoint2(const V2 (&lam)[19], const Pairs2 &P, V2 tau0, float csm18,
+                                                 V2 lux, V2 luy, V2 (&lp)[19]) {
+    const V2 *s = P.s;
+    // ---- forward values ----
+    const V2 rho = P.rho, irho = vrcp(rho);
+    const V2 rux = P.jx, ruy = P.jy, ruz = P.jz;
+    const V2 ux = rux * irho, uy = ruy * irho, uz = ruz * irho;
+    const V2 uxx = rux * ux, uyy = ruy * uy, uzz = ruz * uz;
+    const V2 usq = (uxx + uyy) + uzz;
+    const V2 n1 = vfma(-19.0f, usq, vfma(11.0f, rho, vfma(-30.0f, P.f9, vfma(8.0f, P.Sdg, -11.0f * P.Sax))));
+    const V2 pxx_eq = vfma(2.0f, uxx, -(uyy + uzz)), pww_eq = uyy - uzz;
+    const V2 t1357 = P.s13 + P.s57;
+    const V2 n9 = vfma(2.0f, s[8] - P.s04, t1357 - P.s26) - pxx_eq;
+    const V2 n11 = (s[6] - s[2]) + (P.s57 - P.s13) - pww_eq;
+    const V2 n13 = (s[5] - s[7]) - rux * uy;
+    const V2 n14 = (s[0] - s[4]) - ruy * uz;
+    const V2 n15 = (s[1] - s[3]) - rux * uz;
+    const V2 c2 = n1 * (1.0f / 57.0f);
+    const V2 pxx = vfma(1.0f / 3.0f, n9, c2);
+    const V2 pyz = vfma(-1.0f / 6.0f, n9, c2);
+    const V2 pyy = vfma(0.5f, n11, pyz), pzz = vfma(-0.5f, n11, pyz);
+    V2 qq = vfma(pxx, pxx, vfma(pyy, pyy, pzz * pzz));
+    qq = vfma(2.0f * n13, n13, vfma(2.0f * n14, n14, vfma(2.0f * n15, n15, qq)));
+    const V2 Qh = vsqrt(qq);
+    const V2 Rr = vsqrt(vfma(csm18 * Qh, irho, tau0 * tau0));
+    const V2 sv = 2.0f * vrcp(tau0 + Rr);
+    // ---- mu = M lambda ----
+    V2 ls[9], ld[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) { ls[p] = lam[p] + lam[18 - p]; ld[p] = lam[p] - lam[18 - p]; }
+    const V2 l9 = lam[9];
+    const V2 L04 = ls[0] + ls[4], L13 = ls[1] + ls[3], L57 = ls[5] + ls[7], L26 = ls[2] + ls[6];
+    const V2 LSax = L26 + ls[8], LSdg = (L04 + L13) + L57;
+    const V2 m1 = vfma(-30.0f, l9, vfma(8.0f, LSdg, -11.0f * LSax));
+    const V2 m2 = vfma(12.0f, l9, vfma(-4.0f, LSax, LSdg));
+    const V2 DX = (ld[3] - ld[1]) + (ld[7] - ld[5]);
+    const V2 DY = (ld[4] - ld[0]) - (ld[5] + ld[7]);
+    const V2 DZ = -(ld[0] + ld[4]) - (ld[1] + ld[3]);
+    const V2 m4 = vfma(4.0f, ld[8], DX), m6 = vfma(4.0f, ld[6], DY), m8 = vfma(4.0f, ld[2], DZ);
+    const V2 m9 = vfma(2.0f, ls[8] - L04, (L13 + L57) - L26);
+    const V2 m10 = vfma(-4.0f, ls[8], vfma(2.0f, L26 - L04, L13 + L57));
+    const V2 m11 = (ls[6] - ls[2]) + (L57 - L13);
+    const V2 m12 = vfma(2.0f, ls[2] - ls[6], L57 - L13);
+    const V2 m13 = ls[5] - ls[7], m14 = ls[0] - ls[4], m15 = ls[1] - ls[3];
+    const V2 m16 = (ld[1] - ld[3]) + (ld[7] - ld[5]);
+    const V2 m17 = (ld[4] - ld[0]) + (ld[5] + ld[7]);
+    const V2 m18 = (ld[0] + ld[4]) - (ld[1] + ld[3]);
+    // ---- reverse through G_k = s_k n_k / |row_k|^2: a_k = -mu_k ----
+    V2 bn1 = m1 * (-S_E / 2394.0f);
+    const V2 bn2 = m2 * (-S_EPS / 252.0f);
+    const V2 bn4 = m4 * (-S_Q / 40.0f), bn6 = m6 * (-S_Q / 40.0f), bn8 = m8 * (-S_Q / 40.0f);
+    const V2 msv = -sv;
+    V2 bn9 = m9 * msv * (1.0f / 36.0f);
+    const V2 bn10 = m10 * (-S_PI / 72.0f);
+    V2 bn11 = m11 * msv * (1.0f / 12.0f);
+    const V2 bn12 = m12 * (-S_PI / 24.0f);
+    const V2 sv4 = msv * 0.25f;
+    V2 bn13 = m13 * sv4, bn14 = m14 * sv4, bn15 = m15 * sv4;
+    const V2 bn16 = m16 * (-S_M * 0.125f), bn17 = m17 * (-S_M * 0.125f), bn18 = m18 * (-S_M * 0.125f);
+    const V2 bsv = vfma(m9 * n9, vdup(-1.0f / 36.0f),
+                        vfma(m11 * n11, vdup(-1.0f / 12.0f),
+                             (vfma(m13, n13, vfma(m14, n14, m15 * n15))) * -0.25f));
+    // ---- SGS: sv = 2 / (tau0 + sqrt(tau0^2 + c Qh / rho)) ----
+    const V2 lX = bsv * (-0.25f) * sv * sv * vrcp(Rr);
+    const V2 lQh = lX * irho * csm18;
+    V2 lirho = lX * Qh * csm18;
+    const V2 iQh = vrcp(Qh);
+    const V2 lqq = vsel(Qh.x > 1e-30f, Qh.y > 1e-30f, 0.5f * lQh * iQh);
+    const V2 lpxx = 2.0f * pxx * lqq, lpyy = 2.0f * pyy * lqq, lpzz = 2.0f * pzz * lqq;
+    const V2 lqq4 = 4.0f * lqq;
+    bn13 = vfma(n13, lqq4, bn13); bn14 = vfma(n14, lqq4, bn14); bn15 = vfma(n15, lqq4, bn15);
+    const V2 lc2 = ((lpxx + lpyy) + lpzz) * (1.0f / 3.0f);
+    bn9 = bn9 + (lpxx - 0.5f * (lpyy + lpzz)) * (1.0f / 3.0f);
+    bn11 = bn11 + (lpyy - lpzz) * 0.5f;
+    bn1 = vfma(1.0f / 19.0f, lc2, bn1);
+    // ---- n_k -> pair sums / differences, rho, rho u ----
+    V2 lrho = vfma(11.0f, bn1, -3.0f * bn2);
+    const V2 lusq = vfma(-19.0f, bn1, 5.5f * bn2);
+    const V2 lf9 = vfma(-30.0f, bn1, 12.0f * bn2);
+    const V2 lSax = vfma(-11.0f, bn1, -4.0f * bn2), lSdg = vfma(8.0f, bn1, bn2);
+    const V2 b910 = bn9 + bn10, b1112 = bn11 + bn12;
+    V2 las[9], lad[9];
+    las[0] = (lSdg - 2.0f * b910) + bn14;
+    las[4] = (lSdg - 2.0f * b910) - bn14;
+    las[1] = ((lSdg + b910) - b1112) + bn15;
+    las[3] = ((lSdg + b910) - b1112) - bn15;
+    las[5] = ((lSdg + b910) + b1112) + bn13;
+    las[7] = ((lSdg + b910) + b1112) - bn13;
+    las[2] = vfma(2.0f, bn10 + bn12, lSax - (bn9 + bn11));
+    las[6] = vfma(2.0f, bn10 - bn12, (lSax - bn9) + bn11);
+    las[8] = vfma(2.0f, bn9, vfma(-4.0f, bn10, lSax));
+    lad[1] = bn16 - bn18; lad[3] = -(bn16 + bn18);
+    lad[7] = bn16 + bn17; lad[5] = bn17 - bn16;
+    lad[4] = bn17 + bn18; lad[0] = bn18 - bn17;
+    lad[8] = 5.0f * bn4; lad[6] = 5.0f * bn6; lad[2] = 5.0f * bn8;
+    const V2 lpxxeq = vfma(0.5f, bn10, -bn9), lpwweq = vfma(0.5f, bn12, -bn11);
+    const V2 luxx = vfma(2.0f, lpxxeq, lusq), luyy = (lusq - lpxxeq) + lpwweq, luzz = (lusq - lpxxeq) - lpwweq;
+    // uxx = rux ux, uyy = ruy uy, uzz = ruz uz, uxy = rux uy, uyz = ruy uz, uxz = rux uz
+    // with a_uxy = -bn13, a_uyz = -bn14, a_uxz = -bn15; u = ru / rho
+    const V2 lux_ = vfma(rux, luxx, lux);
+    const V2 luy_ = vfma(ruy, luyy, luy) - rux * bn13;
+    const V2 luz_ = vfma(ruz, luzz, -(ruy * bn14 + rux * bn15));
+    V2 lrux = vfma(2.0f / 3.0f, bn4, vfma(ux, luxx, -(uy * bn13 + uz * bn15)));
+    V2 lruy = vfma(2.0f / 3.0f, bn6, vfma(uy, luyy, -(uz * bn14)));
+    V2 lruz = vfma(2.0f / 3.0f, bn8, uz * luzz);
+    lrux = vfma(irho, lux_, lrux); lruy = vfma(irho, luy_, lruy); lruz = vfma(irho, luz_, lruz);
+    lirho = lirho + vfma(rux, lux_, vfma(ruy, luy_, ruz * luz_));
+    lrho = lrho - irho * irho * lirho;
+    // j = momentum sum: n4 = jx + ..., so a_jx = bn4 + a_rux (rux = jx here)
+    const V2 ljx = bn4 + lrux, ljy = bn6 + lruy, ljz = bn8 + lruz;
+    // ---- to the populations: rho = sum f, j from the differences ----
+    lad[3] = lad[3] + ljx - ljz; lad[1] = lad[1] - ljx - ljz; lad[7] = lad[7] + ljx - ljy; lad[5] = lad[5] - ljx - ljy;
+    lad[8] = lad[8] - ljx;
+    lad[4] = lad[4] + ljy - ljz; lad[0] = lad[0] - ljy - ljz; lad[6] = lad[6] - ljy;
+    lad[2] = lad[2] - ljz;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const V2 a = las[p] + lrho;
+        lp[p] = (lam[p] + a) + lad[p];
+        lp[18 - p] = (lam[18 - p] + a) - lad[p];
+    }
+    lp[9] = (lam[9] + lf9) + lrho;
+}
+
+template <bool SPONGE>
+__device__ __forceinline__ void adjoint_pair(const AdjArgs &a, int i0, int j, int k) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long N = (long long)nx * ny * nz;
+    // pull geometry (interior row, no wall mirror); x wraps when the inlet is off
+    int xm0 = i0 - 1, xp1 = i0 + 2;
+    if (!a.inlet) { xm0 = xm0 < 0 ? nx - 1 : xm0; xp1 = xp1 >= nx ? 0 : xp1; }
+    const int plane = nx * ny;
+    const int ozm = k == 0 ? (nz - 1) * plane : -plane;
+    const int ozp = k == nz - 1 ? -(nz - 1) * plane : plane;
+    const int o00 = (k * ny + j) * nx;
+    auto row = [&](int q) {
+        return o00 + (CY(q) < 0 ? nx : (CY(q) > 0 ? -nx : 0)) + (CZ(q) < 0 ? ozp : (CZ(q) > 0 ? ozm : 0));
+    };
+    V2 f[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const float *r = a.in[q] + row(q);
+        if (CX(q) == 0) f[q] = *reinterpret_cast<const float2 *>(r + i0);
+        else if (CX(q) > 0) f[q] = make_float2(r[xm0], r[i0]);
+        else f[q] = make_float2(r[i0 + 1], r[xp1]);
+    }
+    Pairs2 P;
+    make_pairs2<false>(f, P);
+    V2 lam[19];
+    const int c = o00 + i0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) lam[q] = *reinterpret_cast<const float2 *>(a.lam + q * N + c);
+    V2 lux = vdup(0.0f), luy = vdup(0.0f);
+    if (a.jr_coef && (i0 == a.i_R || i0 + 1 == a.i_R)) {
+        // J_R: d/du of the <u'v'> terms, u and v of this collision
+        const V2 ir = vrcp(P.rho);
+        const V2 uu = P.jx * ir, vv = P.jy * ir;
+        const float cj = a.jr_coef[j];
+        const bool lo = i0 == a.i_R;
+        lux = vsel(lo, !lo, cj * (vv - vdup(a.jr_mean[ny + j])));
+        luy = vsel(lo, !lo, cj * (uu - vdup(a.jr_mean[j])));
+    }
+    const V2 t0c = SPONGE ? make_float2(sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, i0),
+                                        sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, i0 + 1))
+                          : vdup(a.tau0);
+    V2 lp[19];
+    collide_adjoint2(lam, P, t0c, a.csm18, lux, luy, lp);
+    // push to the pull sources (a permutation for these cells)
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        float *r = a.lout + q * N + row(q);
+        if (CX(q) == 0) *reinterpret_cast<float2 *>(r + i0) = lp[q];
+        else if (CX(q) > 0) { r[xm0] = lp[q].x; r[i0] = lp[q].y; }
+        else { r[i0 + 1] = lp[q].x; r[xp1] = lp[q].y; }
+    }
+}
+
+// Rows 2 .. ny-3 with two cells per thread (nx even): block (64, BY) covers
+// 128 cells of two rows.  With the inlet on, the pairs at x = 0 and x = nx-2
+// are left to adjoint_edge_kernel (their cells take the per-cell path), so
+// this kernel holds only the packed code.
+#ifndef LBM_ADJ2_MINB
+#define LBM_ADJ2_MINB 4
+#endif
+template <bool SPONGE>
+__global__ void __launch_bounds__(128, LBM_ADJ2_MINB) adjoint2_kernel(const __grid_constant__ AdjArgs a) {
+    const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = 2 + blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i0 >= a.nx || (a.inlet && (i0 == 0 || i0 + 2 >= a.nx))) return;
+    adjoint_pair<SPONGE>(a, i0, j, k);
+}
+
+// The cells adjoint2_kernel leaves out when the inlet is on: x = 0, 1 (the
+// inlet cell and its pair) and x = nx-2, nx-1 (the outlet's shared reads),
+// rows 2 .. ny-3, one cell per thread.  Its writes are disjoint from the
+// packed kernel's (the shared outlet entries take atomics).
+template <bool SPONGE>
+__global__ void __launch_bounds__(128) adjoint_edge_kernel(const __grid_constant__ AdjArgs a) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows = a.ny - 4;
+    if (e >= 4 * rows * a.nz) return;
+    const int c = e % 4, r = e / 4;
+    const int i = c < 2 ? c : a.nx - 4 + c;
+    adjoint_cell<false, SPONGE>(a, i, 2 + r % rows, r / rows, 0, nullptr);
+}
+
+// ---------------------------------------------------------------------------
 // theta gradient through the inlet velocity, u_in = U_R(j; kappa, B) +
 // amp a(j) v'(j, k, t; ell_e) (eq:u_couple, eq:v_fluc, eq:aux_vec):
 //   dJ/d amp   += luin . (a v'),            dJ/d ell_e += luin . (amp a dv'/d ell_e),

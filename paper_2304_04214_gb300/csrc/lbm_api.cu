@@ -26,14 +26,27 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// Carves one device allocation into 256-byte aligned buffers.  With guard
+// bands on (guard > 0, a debugging aid), a band of at least `guard` bytes sits
+// before the first buffer and right after the end of every buffer (up to the
+// next aligned start); their (offset, bytes) are recorded in *bands.
 struct Arena {
     char *base = nullptr;
     size_t off = 0;
+    size_t guard = 0;
+    std::vector<std::pair<size_t, size_t>> *bands = nullptr;
+    void band() {
+        const size_t start = off;
+        off = (off + guard + 255) & ~size_t(255);
+        if (bands) bands->push_back({start, off - start});
+    }
     template <class T>
     T *take(size_t count) {
+        if (guard && off == 0) band();
         off = (off + 255) & ~size_t(255);
         T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
         off += count * sizeof(T);
+        if (guard) band();
         return p;
     }
 };
@@ -95,6 +108,9 @@ struct AdjointWork {
 struct lbm_handle {
     int nx = 0, ny = 0, nz = 0;
     long long ncell = 0;
+    // x-slab of a larger channel (lbm_set_slab): global length, global x of
+    // local column 0, owned local columns [own_lo, own_hi)
+    int nx_global = 0, x_offset = 0, own_lo = 0, own_hi = 0;
     double re_tau = 0;
     lbm_opts opts{};
     int n_modes = 0;
@@ -108,7 +124,14 @@ struct lbm_handle {
     std::vector<float> sqsig;                 // [ny][N] x (sqrt(6 q), sigma)
     std::vector<uint32_t> alpha, beta, betaT, phi32;
     std::vector<uint64_t> rate64;
+    // row base of the BF16 storage, [ny][RB_W]: f^eq_q(1, (U0(j), 0, 0)) - w_q
+    // with U0 the inlet mean profile of creation (fixed for the handle's life:
+    // the stored words are relative to it)
+    std::vector<float> rowbase;
     // device
+    int device = -1;                      // CUDA device of the bound memory (lbm_bind_memory)
+    size_t guard_bytes = 0;               // guard bands between arena buffers (lbm_debug_guard_bands)
+    std::vector<std::pair<size_t, size_t>> guards, adj_guards;   // (offset, bytes) of the bands
     bool bound = false, owns = false;
     void *mem = nullptr;
     size_t mem_bytes = 0;
@@ -122,6 +145,7 @@ struct lbm_handle {
     int prof_cur = 0;                           // the buffer in use
     float4 *d_sqsig = nullptr;
     uint32_t *d_alpha = nullptr, *d_betaT = nullptr, *d_phi32 = nullptr;
+    float *d_rowbase = nullptr;
     // STG ring, two halves of stg_ring time levels: the half in use holds the
     // inlet fluctuations of steps [stg_t0, stg_t0 + stg_len); the other one is
     // refilled on the aux stream, beside those steps, for the steps from
@@ -215,8 +239,26 @@ struct lbm_handle {
         d_betaT = ar.take<uint32_t>((size_t)nz * N);
         d_phi32 = ar.take<uint32_t>(N);
         d_rate64 = ar.take<uint64_t>(N);
+        d_rowbase = ar.take<float>((size_t)lbmk::RB_W * ny);
         return (ar.off + 255) & ~size_t(255);
     }
+
+    // Row base of the BF16 storage from the current (creation-time) mean profile.
+    void make_rowbase() {
+        static const int cx[19] = {0, -1, 0, 1, 0, -1, 0, 1, -1, 0, 1, -1, 0, 1, 0, -1, 0, 1, 0};
+        static const double w[19] = {1. / 36, 1. / 36, 1. / 18, 1. / 36, 1. / 36, 1. / 36, 1. / 18,
+                                     1. / 36, 1. / 18, 1. / 3,  1. / 18, 1. / 36, 1. / 18, 1. / 36,
+                                     1. / 36, 1. / 36, 1. / 18, 1. / 36, 1. / 36};
+        rowbase.assign((size_t)lbmk::RB_W * ny, 0.f);
+        for (int j = 0; j < ny; ++j) {
+            const double u = prof_U[j];
+            for (int q = 0; q < 19; ++q) {
+                const double cu = cx[q] * u;
+                rowbase[(size_t)j * lbmk::RB_W + q] = (float)(w[q] * (3.0 * cu + 4.5 * cu * cu - 1.5 * u * u));
+            }
+        }
+    }
+    float rb(int j, int q) const { return rowbase[(size_t)j * lbmk::RB_W + q]; }
 
     // Flow constants (A20): U_b+ = mean of u+ over the cell centres with the
     // creation-time (kappa, B); u_tau = U_b / U_b+, nu = u_tau delta / Re_tau.
@@ -477,6 +519,7 @@ struct lbm_handle {
 #define UP(dst, vec) if ((e = cudaMemcpyAsync(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return e
         UP(d_UR, UR); UP(d_amat, amat); UP(d_sqsig, sqsig);
         UP(d_alpha, alpha); UP(d_betaT, betaT); UP(d_phi32, phi32); UP(d_rate64, rate64);
+        UP(d_rowbase, rowbase);
 #undef UP
         (void)N;
         return cudaStreamSynchronize(stream);   // host vectors may change after return
@@ -491,7 +534,32 @@ int cuda_fail(cudaError_t e) {
     return LBM_ECUDA;
 }
 
+// Makes the handle's device current for the length of a call and puts the
+// caller's device back afterwards (a no-op before lbm_bind_memory, or when the
+// handle's device is already current).
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(const lbm_handle *h) {
+        if (!h || h->device < 0) return;
+        int cur = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); ok = false; return; }
+        if (cur == h->device) return;
+        if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); ok = false; return; }
+        prev = cur;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+#define LBM_DEVICE_GUARD(h)                 \
+    DeviceGuard device_guard_(h);           \
+    if (!device_guard_.ok) return LBM_ECUDA
+
 constexpr size_t kEventPool = 2048;
+constexpr int kGuardByte = 0xA5;          // fill of the guard bands
 
 // Harvest a finished event pair into the running total.
 void prof_harvest(lbm_handle *h, size_t slot) {
@@ -631,7 +699,7 @@ cudaError_t launch_staged(lbm_handle *h, const lbmk::StepArgs<S> &a, const void 
 // The outlet sponge as kernel arguments: zone start, 1 / length, 3 nu_s.
 void sponge_args(const lbm_handle *h, float &x0, float &inv, float &s3nu) {
     const int L = h->sponge_cells;
-    x0 = (float)(h->nx - L);
+    x0 = (float)(h->nx_global - L - h->x_offset);     // zone start in local columns
     inv = L > 0 ? 1.0f / (float)L : 0.0f;
     s3nu = L > 0 ? (float)(3.0 * h->sponge_nu) : 0.0f;
 }
@@ -653,6 +721,7 @@ cudaError_t launch_step_t(lbm_handle *h, const StepIO &io) {
     a.fw = io.fw;
     a.ubuf = h->d_ubuf;
     a.flags = h->d_flags;
+    a.rowbase = h->d_rowbase;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
     a.inlet = h->opts.inlet; a.wall_model = h->opts.wall_model;
     a.check = (h->t % h->check_every) == 0;
@@ -849,10 +918,23 @@ void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lou
     const dim3 gw(nbx, 2, h->nz), gi(nbx, (h->ny - 4) / lbmk::BY, h->nz);
     if (sponge) lbmk::adjoint_wall_kernel<true><<<gw, block, 0, h->side>>>(a);
     else lbmk::adjoint_wall_kernel<false><<<gw, block, 0, h->side>>>(a);
+    const bool packed = h->nx % 2 == 0;
+    if (packed && h->opts.inlet && h->ny > 4) {   // the inlet and outlet columns of the interior rows
+        const int ne = 4 * (h->ny - 4) * h->nz;
+        if (sponge) lbmk::adjoint_edge_kernel<true><<<(ne + 127) / 128, 128, 0, h->side>>>(a);
+        else lbmk::adjoint_edge_kernel<false><<<(ne + 127) / 128, 128, 0, h->side>>>(a);
+        h->launches += 1;
+    }
     cudaEventRecord(h->ev_join, h->side);
     if (h->ny > 4) {
-        if (sponge) lbmk::adjoint_kernel<true><<<gi, block, 0, h->stream>>>(a);
-        else lbmk::adjoint_kernel<false><<<gi, block, 0, h->stream>>>(a);
+        if (packed) {                            // two cells per thread, packed arithmetic
+            const dim3 g2((h->nx / 2 + bx - 1) / bx, (h->ny - 4) / lbmk::BY, h->nz);
+            if (sponge) lbmk::adjoint2_kernel<true><<<g2, block, 0, h->stream>>>(a);
+            else lbmk::adjoint2_kernel<false><<<g2, block, 0, h->stream>>>(a);
+        } else {
+            if (sponge) lbmk::adjoint_kernel<true><<<gi, block, 0, h->stream>>>(a);
+            else lbmk::adjoint_kernel<false><<<gi, block, 0, h->stream>>>(a);
+        }
     }
     cudaStreamWaitEvent(h->stream, h->ev_join, 0);
     h->launches += 2;
@@ -876,7 +958,7 @@ template <class S>
 void launch_init(lbm_handle *h, void *lat) {
     const long long n = h->ncell;
     lbmk::init_kernel<S><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>((typename S::T *)lat, h->d_UR,
-                                                                               h->nx, h->ny, n);
+                                                                               h->d_rowbase, h->nx, h->ny, n);
 }
 
 const double kW[19] = {1. / 36, 1. / 36, 1. / 18, 1. / 36, 1. / 36, 1. / 36, 1. / 18, 1. / 36, 1. / 18, 1. / 3,
@@ -1080,6 +1162,7 @@ int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg, c
     if (!h) return LBM_ENOMEM;
     h->nx = grid->nx; h->ny = grid->ny; h->nz = grid->nz;
     h->ncell = (long long)h->nx * h->ny * h->nz;
+    h->nx_global = h->nx; h->x_offset = 0; h->own_lo = 0; h->own_hi = h->nx;
     h->re_tau = re_tau;
     h->opts = *opts;
     h->stream = (cudaStream_t)opts->cuda_stream;
@@ -1093,6 +1176,7 @@ int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg, c
     h->elem = opts->precision == LBM_FP32 ? 4 : 2;
     h->constants();
     h->tables();
+    h->make_rowbase();
     *out = h;
     return LBM_OK;
 }
@@ -1100,6 +1184,7 @@ int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg, c
 int lbm_required_bytes(const lbm_handle *h, size_t *bytes) {
     if (!h || !bytes) return LBM_EINVAL;
     Arena ar;
+    ar.guard = h->guard_bytes;
     lbm_handle tmp_view = *h;   // layout() only writes pointers of the copy
     *bytes = tmp_view.layout(ar);
     return LBM_OK;
@@ -1110,9 +1195,25 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
     if (h->bound) return LBM_ESTATE;
     size_t need = 0;
     lbm_required_bytes(h, &need);
+    // the handle lives on the device of its memory from here on: every later
+    // call makes that device current while it runs
+    int dev = -1;
     if (dev_ptr) {
         if (((uintptr_t)dev_ptr & 255) != 0) return LBM_EINVAL;
         if (bytes < need) return LBM_ENOMEM;
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, dev_ptr) != cudaSuccess ||
+            (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return LBM_EINVAL;                   // not device memory
+        }
+        dev = pa.device;
+    } else if (cudaGetDevice(&dev) != cudaSuccess) {
+        return cuda_fail(cudaGetLastError());
+    }
+    h->device = dev;
+    LBM_DEVICE_GUARD(h);
+    if (dev_ptr) {
         h->mem = dev_ptr;
         h->owns = false;
     } else {
@@ -1143,10 +1244,16 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
     }
     Arena ar;
     ar.base = (char *)h->mem;
+    ar.guard = h->guard_bytes;
+    h->guards.clear();
+    ar.bands = &h->guards;
     h->layout(ar);
     h->bound = true;
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->mem, 0, need, h->stream)) != cudaSuccess) return cuda_fail(e);
+    for (const auto &b : h->guards)
+        if ((e = cudaMemsetAsync((char *)h->mem + b.first, kGuardByte, b.second, h->stream)) != cudaSuccess)
+            return cuda_fail(e);
     if ((e = h->upload_tables()) != cudaSuccess) return cuda_fail(e);
     std::vector<float> ut(2 * (size_t)h->nz * h->nx, (float)h->utau_ref);
     if ((e = cudaMemcpyAsync(h->d_utau, ut.data(), ut.size() * 4, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
@@ -1164,6 +1271,7 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
 
 int lbm_step(lbm_handle *h, int n) {
     if (!h || n < 0) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     for (int s = 0; s < n;) {
         if (graph_usable(h) && n - s >= h->stg_ring) {
@@ -1180,6 +1288,7 @@ int lbm_step(lbm_handle *h, int n) {
 
 int lbm_sync(lbm_handle *h) {
     if (!h) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     unsigned fl[3] = {0, 0, 0};
     cudaError_t e;
@@ -1218,6 +1327,7 @@ int lbm_set_graphs(lbm_handle *h, int on) {
 
 int lbm_probe_wait_timeout(lbm_handle *h) {
     if (!h) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     lbmk::wait_timeout_probe_kernel<<<1, 32, 0, h->stream>>>(h->d_flags, 1 << 14);
     h->launches += 1;
@@ -1238,11 +1348,77 @@ int lbm_get_step_kernel(const lbm_handle *h, int *kind) {
 }
 
 int lbm_set_sponge(lbm_handle *h, int cells, double nu_max) {
-    if (!h || cells < 0 || cells > h->nx || !(nu_max >= 0.0) || !std::isfinite(nu_max)) return LBM_EINVAL;
+    if (!h || cells < 0 || cells > h->nx_global || !(nu_max >= 0.0) || !std::isfinite(nu_max)) return LBM_EINVAL;
     h->sponge_cells = nu_max > 0.0 ? cells : 0;
     h->sponge_nu = cells > 0 ? nu_max : 0.0;
     ++h->graph_epoch;
     return LBM_OK;
+}
+
+int lbm_set_slab(lbm_handle *h, int nx_global, int x_offset, int own_lo, int own_hi) {
+    if (!h || own_lo < 0 || own_hi > h->nx || own_lo >= own_hi || x_offset < 0 ||
+        x_offset + h->nx > nx_global)
+        return LBM_EINVAL;
+    // the global faces are this slab's lattice ends, or not in it at all
+    if ((x_offset + own_lo == 0) != (own_lo == 0) || (x_offset + own_hi == nx_global) != (own_hi == h->nx))
+        return LBM_EINVAL;
+    h->nx_global = nx_global;
+    h->x_offset = x_offset;
+    h->own_lo = own_lo;
+    h->own_hi = own_hi;
+    ++h->graph_epoch;                            // the sponge position may move
+    return LBM_OK;
+}
+
+int lbm_halo_bytes(const lbm_handle *h, size_t *bytes) {
+    if (!h || !bytes) return LBM_EINVAL;
+    *bytes = 5 * (size_t)h->ny * h->nz * h->elem;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// c_x = -1 and c_x = +1 populations (Sec. 2.1 order)
+constexpr int kQxMinus[5] = {1, 5, 8, 11, 15};
+constexpr int kQxPlus[5] = {3, 7, 10, 13, 17};
+
+int halo_copy(lbm_handle *h, int face, void *buf, bool pack) {
+    if (!h || !buf || (face != LBM_FACE_LEFT && face != LBM_FACE_RIGHT)) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
+    if (!h->bound) return LBM_ESTATE;
+    // left face: the first owned column sends its c_x = -1 populations to the
+    // left neighbour; the ghost column before it receives the neighbour's
+    // c_x = +1 populations.  The right face mirrors that.
+    const bool left = face == LBM_FACE_LEFT;
+    lbmk::HaloArgs a;
+    const int *qs = (left == pack) ? kQxMinus : kQxPlus;
+    for (int p = 0; p < 5; ++p) a.qs[p] = qs[p];
+    a.col = pack ? (left ? h->own_lo : h->own_hi - 1) : (left ? h->own_lo - 1 : h->own_hi);
+    if (a.col < 0 || a.col >= h->nx) return LBM_EINVAL;          // no neighbour on that side
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.ncell = h->ncell;
+    const long long n = 5LL * h->ny * h->nz;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    void *lat = h->lat[h->cur];
+    if (h->elem == 4) {
+        if (pack) lbmk::halo_pack_kernel<float><<<blocks, 256, 0, h->stream>>>((const float *)lat, (float *)buf, a);
+        else lbmk::halo_unpack_kernel<float><<<blocks, 256, 0, h->stream>>>((float *)lat, (const float *)buf, a);
+    } else {
+        if (pack)
+            lbmk::halo_pack_kernel<uint16_t><<<blocks, 256, 0, h->stream>>>((const uint16_t *)lat, (uint16_t *)buf, a);
+        else
+            lbmk::halo_unpack_kernel<uint16_t><<<blocks, 256, 0, h->stream>>>((uint16_t *)lat, (const uint16_t *)buf, a);
+    }
+    h->launches += 1;
+    return cuda_fail(cudaGetLastError());
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_halo_pack(lbm_handle *h, int face, void *dev_buf) { return halo_copy(h, face, dev_buf, true); }
+int lbm_halo_unpack(lbm_handle *h, int face, const void *dev_buf) {
+    return halo_copy(h, face, const_cast<void *>(dev_buf), false);
 }
 
 int lbm_set_stream(lbm_handle *h, void *s) {
@@ -1254,6 +1430,7 @@ int lbm_set_stream(lbm_handle *h, void *s) {
 
 int lbm_stats(lbm_handle *h, double *sums, double *utau_sums, long *n_samples) {
     if (!h || !sums || !utau_sums || !n_samples) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(sums, h->d_st, 7 * sizeof(double) * h->nx * h->ny, cudaMemcpyDeviceToHost,
@@ -1267,6 +1444,7 @@ int lbm_stats(lbm_handle *h, double *sums, double *utau_sums, long *n_samples) {
 
 int lbm_reset_stats(lbm_handle *h) {
     if (!h) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->d_st, 0, 7 * sizeof(double) * h->nx * h->ny, h->stream)) != cudaSuccess)
@@ -1280,6 +1458,7 @@ int lbm_reset_stats(lbm_handle *h) {
 
 int lbm_get_fields(lbm_handle *h, double *rho, double *u) {
     if (!h || !rho || !u) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     // the other lattice is free between steps: use it as scratch (>= 16 B per cell)
     float *drho = (float *)h->lat[h->cur ^ 1];
@@ -1290,15 +1469,15 @@ int lbm_get_fields(lbm_handle *h, double *rho, double *u) {
     switch (h->opts.precision) {
         case LBM_FP16_DEV:
             lbmk::fields_kernel<lbmk::StoreF16><<<blocks, 256, 0, h->stream>>>(
-                (const __half *)h->lat[h->cur], h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
+                (const __half *)h->lat[h->cur], h->d_rowbase, h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
             break;
         case LBM_BF16_DEV:
             lbmk::fields_kernel<lbmk::StoreBF16><<<blocks, 256, 0, h->stream>>>(
-                (const __nv_bfloat16 *)h->lat[h->cur], h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
+                (const __nv_bfloat16 *)h->lat[h->cur], h->d_rowbase, h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
             break;
         default:
             lbmk::fields_kernel<lbmk::StoreF32><<<blocks, 256, 0, h->stream>>>(
-                (const float *)h->lat[h->cur], h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
+                (const float *)h->lat[h->cur], h->d_rowbase, h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
     }
     cudaError_t e;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
@@ -1313,6 +1492,7 @@ int lbm_get_fields(lbm_handle *h, double *rho, double *u) {
 
 int lbm_get_populations(lbm_handle *h, double *f) {
     if (!h || !f) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     const size_t n = 19 * (size_t)h->ncell;
     std::vector<char> buf(n * h->elem);
@@ -1326,13 +1506,16 @@ int lbm_get_populations(lbm_handle *h, double *f) {
         if (h->opts.precision == LBM_FP32) f[idx] = ((const float *)buf.data())[idx];
         else if (h->opts.precision == LBM_FP16_DEV)
             f[idx] = kW[q] + (double)__half2float(((const __half *)buf.data())[idx]);
-        else f[idx] = kW[q] + (double)bf16_to_f32(((const uint16_t *)buf.data())[idx]);
+        else   // f - w as the kernels form it: stored word + row base, in FP32
+            f[idx] = kW[q] + (double)(bf16_to_f32(((const uint16_t *)buf.data())[idx]) +
+                                      h->rb((int)((idx % N) / h->nx % h->ny), q));
     }
     return LBM_OK;
 }
 
 int lbm_set_populations(lbm_handle *h, const double *f) {
     if (!h || !f) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     const size_t n = 19 * (size_t)h->ncell, N = h->ncell;
     std::vector<char> buf(n * h->elem);
@@ -1341,7 +1524,9 @@ int lbm_set_populations(lbm_handle *h, const double *f) {
         if (h->opts.precision == LBM_FP32) ((float *)buf.data())[idx] = (float)f[idx];
         else if (h->opts.precision == LBM_FP16_DEV)
             ((__half *)buf.data())[idx] = __double2half(f[idx] - kW[q]);
-        else ((uint16_t *)buf.data())[idx] = f32_to_bf16_rn((float)(f[idx] - kW[q]));
+        else
+            ((uint16_t *)buf.data())[idx] =
+                f32_to_bf16_rn((float)(f[idx] - kW[q] - (double)h->rb((int)((idx % N) / h->nx % h->ny), q)));
     }
     cudaError_t e;
     if ((e = cudaMemcpyAsync(h->lat[h->cur], buf.data(), n * h->elem, cudaMemcpyHostToDevice, h->stream)) !=
@@ -1351,6 +1536,7 @@ int lbm_set_populations(lbm_handle *h, const double *f) {
 
 int lbm_get_utau(lbm_handle *h, double *utau) {
     if (!h || !utau) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     const size_t n = 2 * (size_t)h->nz * h->nx;
     std::vector<float> buf(n);
@@ -1382,6 +1568,7 @@ int lbm_get_constants(const lbm_handle *h, double out[6]) {
 
 int lbm_inlet_velocity(lbm_handle *h, long t, double *out) {
     if (!h || !out || t < 0) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     h->stg_reset();                              // the call writes into the ring
     launch_stg(h, t, 1, true);
@@ -1398,6 +1585,7 @@ int lbm_inlet_velocity(lbm_handle *h, long t, double *out) {
 
 int lbm_set_params(lbm_handle *h, const double theta[4]) {
     if (!h || !theta) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!(theta[0] > 0) || !(theta[2] > 0)) return LBM_EINVAL;
     for (int c = 0; c < 4; ++c) h->theta[c] = theta[c];
     h->tables();
@@ -1409,6 +1597,7 @@ int lbm_set_params(lbm_handle *h, const double theta[4]) {
 
 int lbm_set_inlet_profile(lbm_handle *h, const double *U, const double *R) {
     if (!h || !U || !R) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     std::vector<double> oldU = h->prof_U, oldR = h->prof_R;
     h->prof_U.assign(U, U + h->ny);
     h->prof_R.assign(R, R + 6 * (size_t)h->ny);
@@ -1463,6 +1652,7 @@ extern "C" {
 
 int lbm_wall_shear_async(lbm_handle *h, double *out) {
     if (!h || !out) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     const int n = 2 * h->nx;
     // page-locked host memory the device can address: the reduction stores
@@ -1496,6 +1686,8 @@ int lbm_wall_shear_async(lbm_handle *h, double *out) {
 }
 
 int lbm_wall_shear(lbm_handle *h, double *out) {
+    if (!h || !out) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     const int rc = lbm_wall_shear_async(h, out);
     if (rc) return rc;
     return cuda_fail(cudaStreamSynchronize(h->stream));
@@ -1516,15 +1708,16 @@ double *g_noalloc_ptr[kMaxDevices] = {};
 
 int lbm_wall_shear_noalloc(lbm_handle *h, double *out) {
     if (!h || !out) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     if (h->nx > LBM_NOALLOC_MAX_NX) {
         std::fprintf(stderr, "liblbm_gb300: lbm_wall_shear_noalloc: nx = %d exceeds the fixed scratch "
                      "(LBM_NOALLOC_MAX_NX = %d)\n", h->nx, LBM_NOALLOC_MAX_NX);
         return LBM_ENOSCRATCH;
     }
-    int dev = 0;
+    // the array's address on the handle's device (made current by the guard)
+    const int dev = h->device;
     cudaError_t e;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
     if (dev < 0 || dev >= kMaxDevices) return LBM_EINVAL;
     double *scratch;
     {
@@ -1546,8 +1739,40 @@ int lbm_wall_shear_noalloc(lbm_handle *h, double *out) {
     return cuda_fail(cudaStreamSynchronize(h->stream));
 }
 
+int lbm_debug_guard_bands(lbm_handle *h, int bytes) {
+    if (!h || bytes < 0) return LBM_EINVAL;
+    if (h->bound) return LBM_ESTATE;
+    h->guard_bytes = (size_t)bytes;
+    return LBM_OK;
+}
+
+int lbm_debug_check_guards(lbm_handle *h, long long *changed) {
+    if (!h || !changed) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
+    if (!h->bound) return LBM_ESTATE;
+    cudaError_t e;
+    for (cudaStream_t st : {h->stream, h->side, h->aux, h->copy})
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+    long long bad = 0;
+    std::vector<unsigned char> buf;
+    auto scan = [&](void *base, const std::vector<std::pair<size_t, size_t>> &bands) -> cudaError_t {
+        for (const auto &b : bands) {
+            buf.resize(b.second);
+            cudaError_t err = cudaMemcpy(buf.data(), (char *)base + b.first, b.second, cudaMemcpyDeviceToHost);
+            if (err != cudaSuccess) return err;
+            for (unsigned char c : buf) bad += c != kGuardByte;
+        }
+        return cudaSuccess;
+    };
+    if ((e = scan(h->mem, h->guards)) != cudaSuccess) return cuda_fail(e);
+    if (h->adj.bound && (e = scan(h->adj.mem, h->adj_guards)) != cudaSuccess) return cuda_fail(e);
+    *changed = bad;
+    return LBM_OK;
+}
+
 int lbm_profile_enable(lbm_handle *h, int on) {
     if (!h || on < 0) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (on && h->ev0.empty()) {
         h->ev0.resize(kEventPool); h->ev1.resize(kEventPool); h->ev_busy.assign(kEventPool, 0);
         for (size_t c = 0; c < kEventPool; ++c) {
@@ -1563,6 +1788,7 @@ int lbm_profile_enable(lbm_handle *h, int on) {
 
 int lbm_profile_read(lbm_handle *h, double *ms_total, long *step_launches, long *all_launches) {
     if (!h || !ms_total || !step_launches || !all_launches) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     for (size_t c = 0; c < h->ev_busy.size(); ++c) prof_harvest(h, c);
     *ms_total = h->prof_ms;
     *step_launches = h->prof_n;
@@ -1576,6 +1802,7 @@ int lbm_profile_read(lbm_handle *h, double *ms_total, long *step_launches, long 
 int lbm_adjoint_required_bytes(const lbm_handle *h, int window, int ckpt_every, size_t *bytes) {
     if (!h || !bytes || window < 1 || ckpt_every < 1 || window % ckpt_every) return LBM_EINVAL;
     Arena ar;
+    ar.guard = h->guard_bytes;
     lbm_handle *m = const_cast<lbm_handle *>(h);
     AdjointWork keep = m->adj;
     *bytes = m->adjoint_layout(ar, window, ckpt_every);
@@ -1585,6 +1812,7 @@ int lbm_adjoint_required_bytes(const lbm_handle *h, int window, int ckpt_every, 
 
 int lbm_adjoint_bind(lbm_handle *h, int window, int ckpt_every, void *dev_ptr, size_t bytes) {
     if (!h || window < 1 || ckpt_every < 1 || window % ckpt_every) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (h->opts.precision != LBM_FP32) return LBM_EINVAL;
     if (!h->bound) return LBM_ESTATE;
     size_t need = 0;
@@ -1602,17 +1830,24 @@ int lbm_adjoint_bind(lbm_handle *h, int window, int ckpt_every, void *dev_ptr, s
     }
     Arena ar;
     ar.base = (char *)mem;
+    ar.guard = h->guard_bytes;
+    h->adj_guards.clear();
+    ar.bands = &h->adj_guards;
     h->adjoint_layout(ar, window, ckpt_every);
     h->adj.mem = mem; h->adj.owns = owns; h->adj.bound = true;
     h->adj.T = window; h->adj.K = ckpt_every;
     cudaError_t e;
     if ((e = cudaMemsetAsync(mem, 0, need, h->stream)) != cudaSuccess) return cuda_fail(e);
+    for (const auto &b : h->adj_guards)
+        if ((e = cudaMemsetAsync((char *)mem + b.first, kGuardByte, b.second, h->stream)) != cudaSuccess)
+            return cuda_fail(e);
     return cuda_fail(h->upload_adjoint_tables());
 }
 
 int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_objective *obj, double *J,
                      double dJ_dtheta[4]) {
     if (!h || !obj || !J || !dJ_dtheta) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     if (!h->adj.bound || h->adj.T != window || h->adj.K != ckpt_every) {
         const int rc = lbm_adjoint_bind(h, window, ckpt_every, nullptr, 0);
@@ -1753,6 +1988,7 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
 
 int lbm_adjoint_state_gradient(lbm_handle *h, double *lambda0) {
     if (!h || !lambda0) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->adj.bound || !h->adj.have_lambda0) return LBM_ESTATE;
     const size_t L = 19 * (size_t)h->ncell;
     std::vector<float> buf(L);
@@ -1766,6 +2002,7 @@ int lbm_adjoint_state_gradient(lbm_handle *h, double *lambda0) {
 
 int lbm_vjp_step(lbm_handle *h, const double *lambda_next, double *lambda_prev, double dtheta[4]) {
     if (!h || !lambda_next || !lambda_prev || !dtheta) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     if (!h->adj.bound) {
         const int rc = lbm_adjoint_bind(h, 1, 1, nullptr, 0);
@@ -1866,6 +2103,7 @@ extern "C" {
 
 int lbm_save(lbm_handle *h, const char *path) {
     if (!h || !path) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     cudaError_t e;
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e);
@@ -1896,7 +2134,9 @@ int lbm_save(lbm_handle *h, const char *path) {
     for (auto &r : pl.dev) {
         for (size_t off = 0; rc == LBM_OK && off < r.second; off += kChunk) {
             const size_t n = std::min(kChunk, r.second - off);
-            if ((e = cudaMemcpy(buf.data(), (char *)r.first + off, n, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            if ((e = cudaMemcpyAsync(buf.data(), (char *)r.first + off, n, cudaMemcpyDeviceToHost, h->stream)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
                 rc = cuda_fail(e);
                 break;
             }
@@ -1920,6 +2160,7 @@ int lbm_save(lbm_handle *h, const char *path) {
 
 int lbm_load(lbm_handle *h, const char *path) {
     if (!h || !path) return LBM_EINVAL;
+    LBM_DEVICE_GUARD(h);
     if (!h->bound) return LBM_ESTATE;
     FILE *fp = std::fopen(path, "rb");
     if (!fp) return LBM_EINVAL;
@@ -1942,7 +2183,7 @@ int lbm_load(lbm_handle *h, const char *path) {
     for (auto &r : pl.dev) dev_bytes += r.second;
     const size_t prof_n = hd.custom_profile ? 7 * (size_t)h->ny : 0;
     if (rc == LBM_OK && hd.payload_bytes != dev_bytes + prof_n * sizeof(double)) rc = LBM_EINVAL;
-    if (rc == LBM_OK && (hd.sponge_cells < 0 || hd.sponge_cells > h->nx || !(hd.sponge_nu >= 0.0))) rc = LBM_EINVAL;
+    if (rc == LBM_OK && (hd.sponge_cells < 0 || hd.sponge_cells > h->nx_global || !(hd.sponge_nu >= 0.0))) rc = LBM_EINVAL;
     std::vector<char> data;
     std::vector<double> prof(prof_n);
     if (rc == LBM_OK) {
@@ -1961,15 +2202,20 @@ int lbm_load(lbm_handle *h, const char *path) {
     }
     std::fclose(fp);
     if (rc) return rc;
+    // nothing the handle enqueued may still run when its state is replaced:
+    // steps, wall rows and wall-shear reductions (side stream), STG refills
+    // (aux) and profile uploads (copy) all write the buffers restored below
+    cudaError_t e;
+    for (cudaStream_t s : {h->stream, h->side, h->aux, h->copy})
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
     // parameters and inlet profile (host tables, uploaded), then the device state
     h->custom_profile = false;
     if ((rc = lbm_set_params(h, hd.theta)) != LBM_OK) return rc;
     if (prof_n && (rc = lbm_set_inlet_profile(h, prof.data(), prof.data() + h->ny)) != LBM_OK) return rc;
-    cudaError_t e;
     size_t off = 0;
     for (auto &r : pl.dev) {
-        if ((e = cudaMemcpy(r.first, data.data() + off, r.second, cudaMemcpyHostToDevice)) != cudaSuccess)
-            return cuda_fail(e);
+        if ((e = cudaMemcpyAsync(r.first, data.data() + off, r.second, cudaMemcpyHostToDevice, h->stream)) !=
+            cudaSuccess) return cuda_fail(e);
         off += r.second;
     }
     h->sponge_cells = hd.sponge_cells;
@@ -1984,6 +2230,7 @@ int lbm_load(lbm_handle *h, const char *path) {
 
 void lbm_destroy(lbm_handle *h) {
     if (!h) return;
+    DeviceGuard device_guard(h);
     // no work of the handle may still run when its memory goes
     if (h->copy) cudaStreamSynchronize(h->copy);
     if (h->aux) cudaStreamSynchronize(h->aux);

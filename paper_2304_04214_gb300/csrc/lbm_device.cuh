@@ -42,15 +42,20 @@ constexpr float S_PI = 1.6f;     // moments 10, 12
 constexpr float S_M = 1.98f;     // moments 16, 17, 18
 
 // ---------------------------------------------------------------------------
-// Storage of one population.  FP32 storage holds f itself; the 16-bit formats
-// hold the deviation f - w_q.  SHIFTED tells the collision which of the two
-// its registers hold (the arithmetic is FP32 either way).
+// Storage of one population.  FP32 storage holds f itself; FP16 holds the
+// deviation f - w_q; BF16 (ROWBASE) holds the deviation from the equilibrium
+// of its row's creation-time mean flow, f - f^eq_q(1, (U0(j), 0, 0)), which in
+// a channel is about ten times smaller than f - w_q, so that BF16's 8
+// significant bits round it ten times less coarsely in absolute terms.
+// SHIFTED tells the collision that its registers hold f - w (the loads add
+// the row base back, the stores take it off); the arithmetic is FP32 always.
 // ---------------------------------------------------------------------------
 // ld2 / st2 move two adjacent populations (even offset) in one access, ld4 /
 // st4 four (offset a multiple of four).
 struct StoreF32 {
     using T = float;
     static constexpr bool SHIFTED = false;
+    static constexpr bool ROWBASE = false;
     static __device__ __forceinline__ float ld(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
     static __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
@@ -61,6 +66,7 @@ struct StoreF32 {
 struct StoreF16 {
     using T = __half;
     static constexpr bool SHIFTED = true;
+    static constexpr bool ROWBASE = false;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ float2 ld2(const __half *p) {
@@ -86,6 +92,7 @@ struct StoreF16 {
 struct StoreBF16 {
     using T = __nv_bfloat16;
     static constexpr bool SHIFTED = true;
+    static constexpr bool ROWBASE = true;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
@@ -524,6 +531,7 @@ struct StepArgs {
     float *__restrict__ fw;                  // [2][nz][nx][3] wall force of this step
     float *__restrict__ ubuf;                // [3][ncell] velocity (statistics steps)
     unsigned *__restrict__ flags;            // [0] Newton failures, [1] divergence
+    const float *__restrict__ rowbase;       // [ny][RB_W] row base of ROWBASE storage (else unused)
     int nx, ny, nz;
     int inlet, wall_model;
     int check;                               // test |u| < 0.3 and finiteness this step
@@ -554,6 +562,47 @@ __device__ __forceinline__ V2 pair_tau0(const StepArgs<S> &a, int i0) {
     return make_float2(cell_tau0(a, i0), cell_tau0(a, i0 + 1));
 }
 
+// ---------------------------------------------------------------------------
+// Row base of ROWBASE storage: rb[j * RB_W + q] = f^eq_q(1, (U0(j), 0, 0)) -
+// w_q, the stored word of plane q in row j being f - w_q - rb.  A pulled
+// population q of a cell in row j comes from row j - c_y(q) of plane q, except
+// through a slip wall, where it comes from plane mirror_y(q) of row j.
+// ---------------------------------------------------------------------------
+constexpr int RB_W = 20;
+template <class S>
+__device__ __forceinline__ float rowbase(const StepArgs<S> &a, int row, int plane) {
+    return S::ROWBASE ? __ldg(a.rowbase + row * RB_W + plane) : 0.0f;
+}
+// pulled populations of interior cells (rows 1 .. ny-2) in row j: add the base back
+template <class S>
+__device__ __forceinline__ void rowbase_decode(const StepArgs<S> &a, V2 (&f)[19], int j) {
+    if constexpr (S::ROWBASE) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q] = f[q] + vdup(rowbase(a, j - CY(q), q));
+    }
+}
+template <class S>
+__device__ __forceinline__ void rowbase_decode(const StepArgs<S> &a, float (&f)[19], int j) {
+    if constexpr (S::ROWBASE) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q] += rowbase(a, j - CY(q), q);
+    }
+}
+// post-collision populations of cells in row j: take the base off before the store
+template <class S>
+__device__ __forceinline__ void rowbase_encode(const StepArgs<S> &a, V2 (&f)[19], int j) {
+    if constexpr (S::ROWBASE) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q] = f[q] - vdup(rowbase(a, j, q));
+    }
+}
+template <class S>
+__device__ __forceinline__ void rowbase_encode(const StepArgs<S> &a, float (&f)[19], int j) {
+    if constexpr (S::ROWBASE) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q] -= rowbase(a, j, q);
+    }
+}
 
 constexpr int BY = 2;  // rows per block: (0,1) and (ny-2,ny-1) share a block
 constexpr int WALL_THREADS = 128;   // threads (x-cells) per block of the wall-row kernel
@@ -677,6 +726,14 @@ __device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k
     float f[19];
     if (bot || top) load_pulled<S, true>(a, f, o00, ozm, ozp, oym, oyp, ic, xm, xp, bot, top);
     else load_pulled<S, false>(a, f, o00, ozm, ozp, oym, oyp, ic, xm, xp, bot, top);
+    if constexpr (S::ROWBASE) {
+        // through a slip wall the population comes mirrored from this row
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const bool mir = (bot && CY(q) > 0) || (top && CY(q) < 0);
+            f[q] += mir ? rowbase(a, j, mirror_y(q)) : rowbase(a, j - CY(q), q);
+        }
+    }
     if (a.inlet && i == 0) inlet_rebuild<S>(a, f, j, k);
     Pairs P;
     make_pairs<S::SHIFTED>(f, P);
@@ -718,6 +775,7 @@ __device__ __noinline__ void wall_rows(const StepArgs<S> &a, int i, int j, int k
     }
     if (a.wall_model && is_wall) collide_mrt<S::SHIFTED, true>(f, P, Fx, Fy, Fz, cell_tau0(a, i), a.csm18, ux, uy, uz);
     else collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, cell_tau0(a, i), a.csm18, ux, uy, uz);
+    rowbase_encode<S>(a, f, j);
     if (valid) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
 }
 
@@ -751,11 +809,13 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, LBM_STEP_MINB) step_kernel(c
     }
     float f[19];
     load_pulled<S, false>(a, f, o00, ozm, ozp, -nx, nx, ic, xm, xp, false, false);
+    rowbase_decode<S>(a, f, j);
     if (a.inlet && i == 0) inlet_rebuild<S>(a, f, j, k);
     Pairs P;
     make_pairs<S::SHIFTED>(f, P);
     float ux, uy, uz;
     collide_mrt<S::SHIFTED, false>(f, P, 0.f, 0.f, 0.f, cell_tau0(a, i), a.csm18, ux, uy, uz);
+    rowbase_encode<S>(a, f, j);
     if (i < nx) finish_cell<S, STATS>(a, f, o00 + i, ux, uy, uz);
 }
 
@@ -830,10 +890,14 @@ __global__ void __launch_bounds__(WALL_THREADS, 4) wall_kernel(const __grid_cons
         const int pb = CY(q) > 0 ? mirror_y(q) : q, pt = CY(q) < 0 ? mirror_y(q) : q;
         const int rb = CY(q) < 0 ? nx : 0, rt = CY(q) > 0 ? -nx : 0;
         f[q] = make_float2(S::ld(a.in[pb] + ob + rb + oz + x), S::ld(a.in[pt] + ot + rt + oz + x));
+        if constexpr (S::ROWBASE)                    // source rows: 0 or 1, ny - 1 or ny - 2
+            f[q] = f[q] + make_float2(rowbase(a, CY(q) < 0 ? 1 : 0, pb), rowbase(a, CY(q) > 0 ? ny - 2 : ny - 1, pt));
         if (a.wall_model) {                          // second cells: rows 1 and ny - 2
             const int ry = -CY(q) * nx;
-            const V2 g = make_float2(S::ld(a.in[q] + ob + nx + ry + oz + x),
-                                     S::ld(a.in[q] + ot - nx + ry + oz + x));
+            V2 g = make_float2(S::ld(a.in[q] + ob + nx + ry + oz + x),
+                               S::ld(a.in[q] + ot - nx + ry + oz + x));
+            if constexpr (S::ROWBASE)
+                g = g + make_float2(rowbase(a, 1 - CY(q), q), rowbase(a, ny - 2 - CY(q), q));
             r2 = r2 + g;
             if (CX(q) > 0) jx2 = jx2 + g;
             if (CX(q) < 0) jx2 = jx2 - g;
@@ -923,6 +987,10 @@ __global__ void __launch_bounds__(WALL_THREADS, 4) wall_kernel(const __grid_cons
         }
     }
     if (!valid) continue;
+    if constexpr (S::ROWBASE) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q] = f[q] - make_float2(rowbase(a, 0, q), rowbase(a, ny - 1, q));
+    }
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         S::st(a.out[q] + ob + i, f[q].x);
@@ -977,6 +1045,7 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, Step2Blocks<S>::value) step2
     const int ozp = k == a.nz - 1 ? -(a.nz - 1) * plane : plane;  // source plane for c_z = -1
     V2 f[19];
     load_pair<S>(a, f, (k * ny + j) * nx, ozm, ozp, ic, xm0, xp1);
+    rowbase_decode<S>(a, f, j);
     if (a.inlet && i0 == 0) {                        // the lo cell is an inlet cell
         float fl[19];
 #pragma unroll
@@ -995,6 +1064,7 @@ __global__ void __launch_bounds__(LBM_STEP_THREADS, Step2Blocks<S>::value) step2
         atomicAdd(a.obj + 3 + 3 * j, (double)(u * v));
     }
     const int c = (k * ny + j) * nx + ic;
+    rowbase_encode<S>(a, f, j);
 #pragma unroll
     for (int q = 0; q < 19; ++q) S::st2(a.out[q] + c, f[q]);
     if (STATS) {
@@ -1060,6 +1130,8 @@ __global__ void __launch_bounds__(64, 2 * LBM_STEP4_MINB) step4_kernel(const __g
     quad(5, rp);       quad(6, rp);        quad(7, rp);        quad(8, o00);       quad(9, o00);
     quad(10, o00);     quad(11, rm);       quad(12, rm);       quad(13, rm);       quad(14, rp + ozm);
     quad(15, o00 + ozm); quad(16, o00 + ozm); quad(17, o00 + ozm); quad(18, rm + ozm);
+    rowbase_decode<S>(a, fa, j);
+    rowbase_decode<S>(a, fb, j);
     if (a.inlet && x0 == 0) {                        // cell x0 is an inlet cell
         float fl[19];
 #pragma unroll
@@ -1073,6 +1145,8 @@ __global__ void __launch_bounds__(64, 2 * LBM_STEP4_MINB) step4_kernel(const __g
     collide_mrt2<S::SHIFTED>(fb, pair_tau0(a, x0 + 2), a.csm18, uxb, uyb, uzb);
     if (!valid) return;
     const int c = o00 + x0;
+    rowbase_encode<S>(a, fa, j);
+    rowbase_encode<S>(a, fb, j);
 #pragma unroll
     for (int q = 0; q < 19; ++q) S::st4(a.out[q] + c, make_float4(fa[q].x, fa[q].y, fb[q].x, fb[q].y));
     if (STATS) {
@@ -1087,6 +1161,34 @@ __global__ void __launch_bounds__(64, 2 * LBM_STEP4_MINB) step4_kernel(const __g
         if (!(ua.x < 0.09f) || !(ua.y < 0.09f) || !(ub.x < 0.09f) || !(ub.y < 0.09f))
             atomicAdd(a.flags + 1, 1u);                  // also catches NaN
     }
+}
+
+// ---------------------------------------------------------------------------
+// Halo of an x-slab (one column, the five populations of one c_x sign):
+// buf[p][k][j] <-> lattice plane qs[p], column `col`.  One thread per (p, j, k).
+// ---------------------------------------------------------------------------
+struct HaloArgs {
+    int qs[5];
+    int col, nx, ny, nz;
+    long long ncell;
+};
+template <class T>
+__global__ void halo_pack_kernel(const T *__restrict__ lat, T *__restrict__ buf, const HaloArgs a) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long plane = (long long)a.ny * a.nz;
+    if (e >= 5 * plane) return;
+    const int p = (int)(e / plane);
+    const long long r = e % plane;                       // k * ny + j
+    buf[e] = lat[(long long)a.qs[p] * a.ncell + r * a.nx + a.col];
+}
+template <class T>
+__global__ void halo_unpack_kernel(T *__restrict__ lat, const T *__restrict__ buf, const HaloArgs a) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long plane = (long long)a.ny * a.nz;
+    if (e >= 5 * plane) return;
+    const int p = (int)(e / plane);
+    const long long r = e % plane;
+    lat[(long long)a.qs[p] * a.ncell + r * a.nx + a.col] = buf[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -1192,7 +1294,8 @@ __global__ void __launch_bounds__(STG_KZ * STG_KT) stg_kernel(const __grid_const
 // Initial state f^eq(1, (U_R(y), 0, 0)) and the diagnostics kernels.
 // ---------------------------------------------------------------------------
 template <class S>
-__global__ void init_kernel(typename S::T *f, const float *UR, int nx, int ny, long long ncell) {
+__global__ void init_kernel(typename S::T *f, const float *UR, const float *rowbase, int nx, int ny,
+                            long long ncell) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const int j = (int)((c / nx) % ny);
@@ -1201,19 +1304,22 @@ __global__ void init_kernel(typename S::T *f, const float *UR, int nx, int ny, l
     for (int q = 0; q < 19; ++q) {
         const float cu = CX(q) * u;
         const float dev = WQ(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * u * u);
-        S::st(f + q * ncell + c, S::SHIFTED ? dev : dev + WQ(q));
+        const float base = S::ROWBASE ? rowbase[j * RB_W + q] : 0.0f;
+        S::st(f + q * ncell + c, S::SHIFTED ? dev - base : dev + WQ(q));
     }
 }
 
 // rho = sum f*, rho u = sum f* c - F/2 of the stored post-collision state
 template <class S>
-__global__ void fields_kernel(const typename S::T *f, const float *fw, float *rho, float *u, int nx,
-                              int ny, int nz, long long ncell) {
+__global__ void fields_kernel(const typename S::T *f, const float *rowbase, const float *fw, float *rho,
+                              float *u, int nx, int ny, int nz, long long ncell) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
+    const int jr = (int)((c / nx) % ny);
     float v[19];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) v[q] = S::ld(f + q * ncell + c) - (S::SHIFTED ? 0.0f : WQ(q));
+    for (int q = 0; q < 19; ++q)
+        v[q] = S::ld(f + q * ncell + c) + (S::ROWBASE ? rowbase[jr * RB_W + q] : 0.0f) - (S::SHIFTED ? 0.0f : WQ(q));
     float dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) { dr += v[q]; jx += CX(q) * v[q]; jy += CY(q) * v[q]; jz += CZ(q) * v[q]; }

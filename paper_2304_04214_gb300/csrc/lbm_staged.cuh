@@ -185,9 +185,12 @@ __global__ void __launch_bounds__(SG_THREADS, StagedCfg<S>::MINB)
                     tma_load_4d(dst + q * G::SLOT, &g.tmap, x, y - CY(q), kz, q, bar);
                 }
             }
-            // copies still in flight land before the block may retire
+            // copies still in flight land before the block may retire; a
+            // drain wait that gives up raises the timeout flag (the step's
+            // output is then invalid and lbm_sync reports LBM_ETIMEOUT)
             for (int m = n - STAGES > 0 ? n - STAGES : 0; m < n; ++m)
-                mbar_wait(smem_u32(&full[m % STAGES]), (uint32_t)(m / STAGES) & 1u);
+                if (!mbar_wait(smem_u32(&full[m % STAGES]), (uint32_t)(m / STAGES) & 1u))
+                    atomicOr(a.flags + 2, 1u);
         }
         return;
     }
@@ -244,6 +247,7 @@ __global__ void __launch_bounds__(SG_THREADS, StagedCfg<S>::MINB)
                 if (CX(q) < 0 && i0 + 2 == nx) f[q].y = S::ld(row);
             }
         }
+        rowbase_decode<S>(a, f, j);
         if (a.inlet && i0 == 0 && valid) {             // the lo cell is an inlet cell
             float fl[19];
 #pragma unroll
@@ -256,6 +260,7 @@ __global__ void __launch_bounds__(SG_THREADS, StagedCfg<S>::MINB)
         collide_mrt2<S::SHIFTED>(f, pair_tau0(a, i0), a.csm18, ux, uy, uz);
         if (!valid) continue;
         const int c = (k * ny + j) * nx + i0;
+        rowbase_encode<S>(a, f, j);
 #pragma unroll
         for (int q = 0; q < 19; ++q) S::st2(a.out[q] + c, f[q]);
         if (STATS) {

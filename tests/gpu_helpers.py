@@ -28,19 +28,33 @@ def make_pair(nx, ny, nz, re_tau=1000.0, n_modes=16, seed=1, precision="fp32", i
     return o, g
 
 
-def quantize_state(f, precision):
-    """Round the deviations f - w to the storage type, so that both sides
-    start from the same exactly representable state."""
+def bf16_row_base(o):
+    """Row base of the BF16 storage, (19, ny) in FP32: f^eq_q(1, (U_R(j), 0, 0))
+    - w_q with the creation-time inlet mean profile U_R of the oracle `o`
+    (the library stores f - w - base and forms f - w in FP32)."""
+    _, w, _ = cell_api.matrix()
+    UR = o.tables()["UR"]
+    base = np.stack([cell_api.feq(1.0, (UR[j], 0.0, 0.0)) - w for j in range(len(UR))], axis=1)
+    return base.astype(np.float32)
+
+
+def quantize_state(f, precision, o=None):
+    """Round the stored deviations to the storage type, so that both sides
+    start from the same exactly representable state: f - w for FP16, f - w -
+    base(j) for BF16 (needs the oracle `o` for its profile)."""
     if precision == "fp32":
         return f.astype(np.float32).astype(np.float64)
     _, w, _ = cell_api.matrix()
     wq = w[:, None, None, None]
-    r = round_to_fp16 if precision == "fp16" else round_to_bf16
-    return wq + r(f - wq)
+    if precision == "fp16":
+        return wq + round_to_fp16(f - wq)
+    b32 = bf16_row_base(o)[:, None, :, None]
+    r = round_to_bf16(f - wq - b32.astype(np.float64))
+    return wq + (r.astype(np.float32) + b32).astype(np.float64)
 
 
 def set_both(o, g, f):
-    f = quantize_state(f, g.precision)
+    f = quantize_state(f, g.precision, o)
     o.set_state(f)
     g.set_populations(f)
     return f

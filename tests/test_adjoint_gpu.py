@@ -35,10 +35,11 @@ def _setup(nx=24, ny=8, nz=4, N=8, seed=21, theta=(0.4, 1.0, 0.4, 7.8), eps=0.01
     return o, g, f0
 
 
-def _oracle_cs(nx, ny, nz, N, seed, theta, f0, fim=None, theta_im=None, steps=1, obj=None):
+def _oracle_cs(nx, ny, nz, N, seed, theta, f0, fim=None, theta_im=None, steps=1, obj=None, t0=0):
     cfg = default_config(nx, ny, nz, n_modes=N, kappa0=theta[2], B0=theta[3])
     oz = Oracle(cfg, theta=theta, uniforms=stg_uniforms(N, seed), complex_step=True, theta_im=theta_im)
     oz.set_state(f0, fim)
+    oz.time = t0
     if obj is not None:
         oz.objective_begin(*obj)
     oz.step(steps)
@@ -125,6 +126,52 @@ def test_adjoint_window_gradient_matches_complex_step():
     ref = oz.objective()[1] / H
     got = np.sum(lam0 * v)
     assert abs(got - ref) <= 1e-3 * abs(ref) + 1e-9, (got, ref)
+
+
+@pytest.mark.parametrize("T,K,t0", [(256, 32, 0), (512, 64, 37)])
+def test_long_adjoint_windows_match_complex_step(T, K, t0):
+    """The window lengths the inlet tuning uses: T steps with a checkpoint
+    every K (K - 1 segment slots recomputed per segment, u_tau of every step,
+    the STG field of the whole window), the second starting at a time that is
+    not a multiple of the STG ring period.  J, the state after the window, all
+    four dJ/dtheta and dJ/ds_0 along a random direction against the oracle."""
+    from paper_2304_04214_gb300 import _abi
+    nx, ny, nz, N, seed, theta = 32, 8, 4, 8, 24, (0.4, 1.0, 0.4, 7.8)
+    obj = (4, 12, 6)
+    o, g, f0 = _setup(nx, ny, nz, N, seed, theta)
+    o.time = t0
+    g.time = t0
+    J = ct.c_double()
+    dJ = np.empty(4)
+    ob = _abi.Objective(*obj)
+    _abi.check(g.lib.lbm_adjoint_step(g.h, T, K, ct.byref(ob), ct.byref(J), _dp(dJ)), "lbm_adjoint_step")
+    lam0 = np.empty((19, nz, ny, nx))
+    _abi.check(g.lib.lbm_adjoint_state_gradient(g.h, _dp(lam0)), "lbm_adjoint_state_gradient")
+    assert g.time == t0 + T
+    o.objective_begin(*obj)
+    o.step(T)
+    Jo = o.objective()[0]
+    assert abs(J.value - Jo) <= 1e-4 * abs(Jo), (J.value, Jo)
+    _, uo = o.fields()
+    _, ug = g.fields()
+    assert np.max(np.abs(ug - uo)) < 1e-3 * np.max(np.abs(uo))
+    for kk in range(4):
+        im = np.zeros(4)
+        im[kk] = H
+        oz = _oracle_cs(nx, ny, nz, N, seed, theta, f0, theta_im=im, steps=T, obj=obj, t0=t0)
+        ref = oz.objective()[1] / H
+        assert abs(dJ[kk] - ref) <= 1e-3 * abs(ref) + 1e-10, (kk, dJ[kk], ref)
+    v = noise((19, nz, ny, nx), seed=42)
+    oz = _oracle_cs(nx, ny, nz, N, seed, theta, f0, fim=H * v, steps=T, obj=obj, t0=t0)
+    ref = oz.objective()[1] / H
+    got = np.sum(lam0 * v)
+    assert abs(got - ref) <= 1e-3 * abs(ref) + 1e-9, (got, ref)
+    # the channel steps on from the window's end like one that never ran it
+    o.step(70)
+    g.step(70)
+    _, uo = o.fields()
+    _, ug = g.fields()
+    assert np.max(np.abs(ug - uo)) < 1e-3 * np.max(np.abs(uo))
 
 
 def test_autograd_function_returns_the_adjoint_gradient():

@@ -76,3 +76,28 @@ def test_bad_files_are_refused_and_change_nothing(tmp_path):
         assert other.lib.lbm_load(other.h, str(good).encode()) == _abi.LBM_EINVAL
     assert b.lib.lbm_load(b.h, str(tmp_path / "missing.lbm").encode()) == _abi.LBM_EINVAL
     assert np.array_equal(b.populations(), before) and b.time == 3
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_load_right_after_steps_needs_no_sync(tmp_path, precision):
+    """lbm_load directly after lbm_step, with the steps (and a wall-shear
+    reduction on the side stream, an STG refill on the second stream) still in
+    flight: the load waits for them, so what it restores is not overwritten
+    and the next steps match the run that saved, bit for bit."""
+    import torch
+    a = _channel(precision)
+    a.step(5)
+    path = tmp_path / "a.lbm"
+    a.save(path)
+    a.step(70)                      # across an STG ring period
+    b = _channel(precision)
+    b.step(130)                     # many steps enqueued, none waited for
+    b.wall_shear_async(torch.empty(2 * b.nx, dtype=torch.float64).pin_memory())
+    b.load(path)
+    b.step(70)
+    assert b.time == 75
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.utau(), b.utau())
+    sa, ua, na = a.stats()
+    sb, ub, nb = b.stats()
+    assert na == nb and np.array_equal(sa, sb) and np.array_equal(ua, ub)
