@@ -351,6 +351,7 @@ def run_native(args, cfg, ws, rank, local):
             torch.distributed.barrier()
 
     # ---- warm-up ----
+    barrier()                                    # (under NCCL: a first collective of all ranks)
     run.step(args.warmup)
     ch.sync()
     barrier()

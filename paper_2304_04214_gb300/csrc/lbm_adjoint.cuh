@@ -215,8 +215,11 @@ __device__ __forceinline__ void adjoint_to_pops(const float (&lam)[19], AdjIn &A
 // R(u) = u u+(y1 u / nu) - uhat; dR/du = u+ + y+ u+'; dR/dkappa = u du+/dkappa; dR/dB = u du+/dB.
 __device__ __forceinline__ void reichardt_partials(float yp, float kap, float B, float &up, float &dup, float &dk,
                                                    float &dB) {
-    const float e11 = expf(-yp * (1.0f / 11.0f)), e3 = expf(-yp * (1.0f / 3.0f));
-    const float l1 = log1pf(kap * yp);
+    // fast exponential / logarithm (kappa y+ >= ~1 at a first cell, where
+    // log(1 + x) loses nothing): errors of a few ulp, far below the 1e-3 of
+    // the gradients
+    const float e11 = __expf(-yp * (1.0f / 11.0f)), e3 = __expf(-yp * (1.0f / 3.0f));
+    const float l1 = __logf(1.0f + kap * yp);
     up = l1 * (1.0f / kap) + B * (1.0f - e11 - yp * (1.0f / 11.0f) * e3);
     dup = rcp_approx(1.0f + kap * yp) + B * (e11 * (1.0f / 11.0f) - e3 * (1.0f / 11.0f) + yp * (1.0f / 33.0f) * e3);
     dk = (-l1 + kap * yp * rcp_approx(1.0f + kap * yp)) * rcp_approx(kap * kap);
@@ -230,7 +233,7 @@ struct AdjArgs {
                                     // once read: the buffer receives atomics in the next adjoint step)
     float *lout;                    // [19][ncell] dJ/ds_n (written by push; its outlet c_x < 0 entries
                                     // must be zero on entry)
-    const float *__restrict__ utau;  // [2][nz][nx] u_tau of this step (forward result, warm start)
+    const float *__restrict__ utau;  // [2][nz][nx] u_tau of this step (the forward step's solution)
     const float *__restrict__ vprime;  // [nz][ny][3] STG field of this step
     const float *__restrict__ UR;
     const float *__restrict__ amat;
@@ -280,10 +283,14 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     G.bot = j == 0; G.top = j == ny - 1;
     G.oym = G.bot ? 0 : -nx; G.oyp = G.top ? 0 : nx;
     G.o00 = (k * ny + j) * nx;
-    // ---- forward recompute: pull ----
-    float f[19];
+    // ---- forward recompute: pull; the cell's lambda is loaded with it, so
+    // that its latency overlaps the recomputation ----
+    float f[19], lam[19];
+    const int c = G.o00 + G.ic;
 #pragma unroll
     for (int q = 0; q < 19; ++q) f[q] = a.in[WALLBLOCK ? src_plane(q, G) : q][src_off(q, G)];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) lam[q] = valid ? a.lam[q * N + c] : 0.0f;
     // ---- inlet rebuild (eq:f_i, eq:bc_eq, eq:f_i_neq, eq:density_bc) ----
     const bool is_inlet = a.inlet && i == 0;
     float vx = 0.f, vy = 0.f, vz = 0.f, rin = 1.f;
@@ -345,11 +352,8 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
                 const float uhat = (P.jx * ex + P.jz * ez) * irho_w;
                 sg = uhat < 0.0f ? -1.0f : 1.0f;
                 const float ua = fabsf(uhat);
-                if (ua > 0.0f && valid) {
-                    bool ok;
-                    const int w = bot ? 0 : 1;
-                    ut = solve_utau_dev(ua, a.y1_nu, a.kappa, a.B, a.utau[((size_t)w * nz + k) * nx + i], &ok);
-                }
+                // the forward step stored this step's solution of eq:u_tau_implicit
+                if (ua > 0.0f && valid) ut = a.utau[((size_t)(bot ? 0 : 1) * nz + k) * nx + i];
                 const float tw = (1.0f + P.drho) * ut * ut * sg;
                 Fx = -tw * ex; Fz = -tw * ez;
             }
@@ -357,10 +361,6 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
         __syncthreads();   // the shared slots are reused for the reverse below
     }
     // ---- reverse of the collision (with the objective seeds) ----
-    float lam[19];
-    const int c = G.o00 + G.ic;
-#pragma unroll
-    for (int q = 0; q < 19; ++q) lam[q] = valid ? a.lam[q * N + c] : 0.0f;
     if (a.inlet && valid && i == nx - 1) {
         // these entries get the atomics of the next (earlier) adjoint step
 #pragma unroll
@@ -709,12 +709,12 @@ __device__ __forceinline__ void adjoint_pair(const AdjArgs &a, int i0, int j, in
         else if (CX(q) > 0) f[q] = make_float2(r[xm0], r[i0]);
         else f[q] = make_float2(r[i0 + 1], r[xp1]);
     }
-    Pairs2 P;
-    make_pairs2<false>(f, P);
     V2 lam[19];
     const int c = o00 + i0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) lam[q] = *reinterpret_cast<const float2 *>(a.lam + q * N + c);
+    Pairs2 P;
+    make_pairs2<false>(f, P);
     V2 lux = vdup(0.0f), luy = vdup(0.0f);
     if (a.jr_coef && (i0 == a.i_R || i0 + 1 == a.i_R)) {
         // J_R: d/du of the <u'v'> terms, u and v of this collision
@@ -740,34 +740,45 @@ __device__ __forceinline__ void adjoint_pair(const AdjArgs &a, int i0, int j, in
     }
 }
 
-// Rows 2 .. ny-3 with two cells per thread (nx even): block (64, BY) covers
-// 128 cells of two rows.  With the inlet on, the pairs at x = 0 and x = nx-2
-// are left to adjoint_edge_kernel (their cells take the per-cell path), so
-// this kernel holds only the packed code.
 #ifndef LBM_ADJ2_MINB
 #define LBM_ADJ2_MINB 4
 #endif
-template <bool SPONGE>
-__global__ void __launch_bounds__(128, LBM_ADJ2_MINB) adjoint2_kernel(const __grid_constant__ AdjArgs a) {
-    const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int j = 2 + blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i0 >= a.nx || (a.inlet && (i0 == 0 || i0 + 2 >= a.nx))) return;
-    adjoint_pair<SPONGE>(a, i0, j, k);
-}
 
-// The cells adjoint2_kernel leaves out when the inlet is on: x = 0, 1 (the
-// inlet cell and its pair) and x = nx-2, nx-1 (the outlet's shared reads),
-// rows 2 .. ny-3, one cell per thread.  Its writes are disjoint from the
-// packed kernel's (the shared outlet entries take atomics).
+// One reverse step in one launch (nx even): blocks [0, nw) do the wall rows
+// and their second rows as adjoint_wall_kernel does, blocks [nw, nw + ne) the
+// inlet and outlet columns of rows 2..ny-3 one cell per thread, and the rest
+// the packed interior pairs.  Blocks start in index order, so the long
+// per-cell chains of the first two parts run beside the interior pairs
+// instead of after them.  Block (64, BY); the parts write disjoint entries
+// (the outlet's shared entries take atomics).
 template <bool SPONGE>
-__global__ void __launch_bounds__(128) adjoint_edge_kernel(const __grid_constant__ AdjArgs a) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int rows = a.ny - 4;
-    if (e >= 4 * rows * a.nz) return;
-    const int c = e % 4, r = e / 4;
-    const int i = c < 2 ? c : a.nx - 4 + c;
-    adjoint_cell<false, SPONGE>(a, i, 2 + r % rows, r / rows, 0, nullptr);
+__global__ void __launch_bounds__(128, LBM_ADJ2_MINB)
+    adjoint_fused_kernel(const __grid_constant__ AdjArgs a, int nw, int ne) {
+    __shared__ float sh[128 / BY][4];
+    const int b = blockIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (b < nw) {                                    // rows 0, 1 and ny-2, ny-1
+        const int nbx = (a.nx + 63) / 64;
+        const int bx = b % nbx, r = b / nbx;
+        const int j = (r % 2) == 0 ? ty : a.ny - 2 + ty;
+        adjoint_cell<true, SPONGE>(a, bx * 64 + tx, j, r / 2, tx, sh);
+        return;
+    }
+    if (b < nw + ne) {                               // x = 0, 1, nx-2, nx-1 of rows 2..ny-3
+        const int e = (b - nw) * 128 + ty * 64 + tx;
+        const int rows = a.ny - 4;
+        if (e >= 4 * rows * a.nz) return;
+        const int c = e % 4, rr = e / 4;
+        adjoint_cell<false, SPONGE>(a, c < 2 ? c : a.nx - 4 + c, 2 + rr % rows, rr / rows, 0, nullptr);
+        return;
+    }
+    const int nb2 = (a.nx / 2 + 63) / 64, rows2 = (a.ny - 4) / BY;
+    const int bi = b - nw - ne;
+    const int bx = bi % nb2, r = bi / nb2;
+    const int i0 = 2 * (bx * 64 + tx);
+    const int j = 2 + (r % rows2) * BY + ty;
+    if (i0 >= a.nx || (a.inlet && (i0 == 0 || i0 + 2 >= a.nx))) return;
+    adjoint_pair<SPONGE>(a, i0, j, r / rows2);
 }
 
 // ---------------------------------------------------------------------------

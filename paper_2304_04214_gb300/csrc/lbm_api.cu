@@ -907,34 +907,33 @@ void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lou
     a.y1_nu = (float)(0.5 / h->nu);
     a.kappa = (float)h->theta[2]; a.B = (float)h->theta[3];
     sponge_args(h, a.sp_x0, a.sp_inv, a.sp_3nu);
-    // wall rows and their second rows on the side stream, the rest on the
-    // handle's stream (disjoint writes), joined before anything that follows
+    const bool sponge = a.sp_3nu != 0.0f;
+    if (h->nx % 2 == 0) {
+        // one launch: wall rows, the inlet / outlet columns, packed interior pairs
+        const int nw = ((h->nx + 63) / 64) * 2 * h->nz;
+        const int ne = h->opts.inlet && h->ny > 4 ? (4 * (h->ny - 4) * h->nz + 127) / 128 : 0;
+        const int ni = h->ny > 4 ? ((h->nx / 2 + 63) / 64) * ((h->ny - 4) / lbmk::BY) * h->nz : 0;
+        const dim3 block(64, lbmk::BY);
+        if (sponge) lbmk::adjoint_fused_kernel<true><<<nw + ne + ni, block, 0, h->stream>>>(a, nw, ne);
+        else lbmk::adjoint_fused_kernel<false><<<nw + ne + ni, block, 0, h->stream>>>(a, nw, ne);
+        h->launches += 1;
+        return;
+    }
+    // odd nx: wall rows and their second rows on the side stream, the rest
+    // (one cell per thread) on the handle's stream, joined before anything
+    // that follows
     const int bx = 64;
     const dim3 block(bx, lbmk::BY);
     const int nbx = (h->nx + bx - 1) / bx;
     cudaEventRecord(h->ev_fork, h->stream);
     cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-    const bool sponge = a.sp_3nu != 0.0f;
     const dim3 gw(nbx, 2, h->nz), gi(nbx, (h->ny - 4) / lbmk::BY, h->nz);
     if (sponge) lbmk::adjoint_wall_kernel<true><<<gw, block, 0, h->side>>>(a);
     else lbmk::adjoint_wall_kernel<false><<<gw, block, 0, h->side>>>(a);
-    const bool packed = h->nx % 2 == 0;
-    if (packed && h->opts.inlet && h->ny > 4) {   // the inlet and outlet columns of the interior rows
-        const int ne = 4 * (h->ny - 4) * h->nz;
-        if (sponge) lbmk::adjoint_edge_kernel<true><<<(ne + 127) / 128, 128, 0, h->side>>>(a);
-        else lbmk::adjoint_edge_kernel<false><<<(ne + 127) / 128, 128, 0, h->side>>>(a);
-        h->launches += 1;
-    }
     cudaEventRecord(h->ev_join, h->side);
     if (h->ny > 4) {
-        if (packed) {                            // two cells per thread, packed arithmetic
-            const dim3 g2((h->nx / 2 + bx - 1) / bx, (h->ny - 4) / lbmk::BY, h->nz);
-            if (sponge) lbmk::adjoint2_kernel<true><<<g2, block, 0, h->stream>>>(a);
-            else lbmk::adjoint2_kernel<false><<<g2, block, 0, h->stream>>>(a);
-        } else {
-            if (sponge) lbmk::adjoint_kernel<true><<<gi, block, 0, h->stream>>>(a);
-            else lbmk::adjoint_kernel<false><<<gi, block, 0, h->stream>>>(a);
-        }
+        if (sponge) lbmk::adjoint_kernel<true><<<gi, block, 0, h->stream>>>(a);
+        else lbmk::adjoint_kernel<false><<<gi, block, 0, h->stream>>>(a);
     }
     cudaStreamWaitEvent(h->stream, h->ev_join, 0);
     h->launches += 2;
