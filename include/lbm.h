@@ -411,10 +411,11 @@ typedef struct {
 
 /* Device bytes of the adjoint workspace for a window of `window` steps with a
  * checkpoint every `ckpt_every` steps (window a multiple of ckpt_every):
- * window/ckpt_every checkpoint lattices, ckpt_every - 1 recomputed lattices, two
- * adjoint lattices, u_tau of every step, the STG field and the inlet adjoint of
- * every step.  No device work.  Errors: LBM_EINVAL for window < 1,
- * ckpt_every < 1 or window not a multiple of ckpt_every. */
+ * window/ckpt_every checkpoint lattices, two sets of ckpt_every - 1 recomputed
+ * lattices (the next segment is recomputed beside the reverse steps of the
+ * current one), two adjoint lattices, u_tau of every step, the STG field and
+ * the inlet adjoint of every step.  No device work.  Errors: LBM_EINVAL for
+ * window < 1, ckpt_every < 1 or window not a multiple of ckpt_every. */
 int lbm_adjoint_required_bytes(const lbm_handle *h, int window, int ckpt_every, size_t *bytes);
 
 /* Bind the adjoint workspace (caller-owned, 256-byte aligned, at least
@@ -426,7 +427,8 @@ int lbm_adjoint_bind(lbm_handle *h, int window, int ckpt_every, void *dev_ptr, s
  * them and its gradient by the hand-written adjoint of the fused step: store
  * s_0 and every ckpt_every-th state, then for each segment in reverse
  * recompute its states from the checkpoint and run the adjoint steps
- * backwards.  *J and dJ_dtheta[4] are host FP64.  dJ/ds_0 is kept for
+ * backwards (for even nx, a segment's recomputation runs on a stream of the
+ * handle beside the reverse steps of the segment after it).  *J and dJ_dtheta[4] are host FP64.  dJ/ds_0 is kept for
  * lbm_adjoint_state_gradient.  Synchronizes.  Errors: LBM_EINVAL for a
  * window or objective range the workspace or the grid does not fit, the
  * common ones otherwise (binds a workspace first if none is bound). */

@@ -267,6 +267,99 @@ __device__ __forceinline__ int src_off(int q, const PullGeom &g) {
     return g.o00 + oy + oz + x;
 }
 
+// Forward recomputation of the regularized inlet of the cell at x = 0 (as
+// inlet_rebuild, with f holding f itself): u_in and rho_in are returned for
+// the reverse.
+__device__ __forceinline__ void adjoint_inlet_forward(const AdjArgs &a, float (&f)[19], int j, int k, float &vx,
+                                                      float &vy, float &vz, float &rin) {
+    const int ny = a.ny;
+    const float *vp = a.vprime + ((size_t)k * ny + j) * 3;
+    const float *m = a.amat + 6 * j;
+    vx = a.UR[j] + m[0] * vp[0];
+    vy = m[1] * vp[0] + m[2] * vp[1];
+    vz = m[3] * vp[0] + m[4] * vp[1] + m[5] * vp[2];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) f[q] -= WQ(q);
+    const float sk = (f[0] + f[2] + f[4] + f[6] + f[9] + f[12] + f[14] + f[16] + f[18])
+                   + 2.0f * (f[1] + f[5] + f[8] + f[11] + f[15]);
+    rin = (1.0f + sk) * rcp_approx(1.0f - vx);
+    const float drin = rin - 1.0f, vv = vx * vx + vy * vy + vz * vz;
+    auto feq = [&](int q) {
+        const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
+        return WQ(q) * (drin + rin * (3.0f * cu + 4.5f * cu * cu - 1.5f * vv));
+    };
+#pragma unroll
+    for (int q = 0; q < 19; ++q) if (CX(q) <= 0) f[q] -= feq(q);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) if (CX(q) > 0) f[q] = f[18 - q];
+    float pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0, tr = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        pxx += CX(q) * CX(q) * f[q]; pyy += CY(q) * CY(q) * f[q]; pzz += CZ(q) * CZ(q) * f[q];
+        pxy += CX(q) * CY(q) * f[q]; pyz += CY(q) * CZ(q) * f[q]; pxz += CX(q) * CZ(q) * f[q];
+        tr += f[q];
+    }
+    pxx -= tr * (1.0f / 3.0f); pyy -= tr * (1.0f / 3.0f); pzz -= tr * (1.0f / 3.0f);
+    const float trp = (pxx + pyy + pzz) * (1.0f / 3.0f);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const float qp = CX(q) * CX(q) * pxx + CY(q) * CY(q) * pyy + CZ(q) * CZ(q) * pzz
+                       + 2.0f * (CX(q) * CY(q) * pxy + CY(q) * CZ(q) * pyz + CX(q) * CZ(q) * pxz) - trp;
+        f[q] = feq(q) + 4.5f * WQ(q) * qp + WQ(q);
+    }
+}
+
+// Reverse of the regularized inlet: lp (adjoint of the rebuilt populations)
+// becomes the adjoint of the pulled ones; dJ/du_in goes to a.luin.  f is
+// scratch.
+__device__ __forceinline__ void adjoint_inlet_reverse(const AdjArgs &a, float (&f)[19], float (&lp)[19], int j,
+                                                      int k, float vx, float vy, float vz, float rin) {
+    const int ny = a.ny;
+    const float vv = vx * vx + vy * vy + vz * vz;
+    // out_q = fe_q + 4.5 w_q (c c : Pi - tr Pi / 3) + w_q
+    float lPxx = 0, lPyy = 0, lPzz = 0, lPxy = 0, lPyz = 0, lPxz = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const float lq = 4.5f * WQ(q) * lp[q];
+        lPxx += (CX(q) * CX(q) - 1.0f / 3.0f) * lq; lPyy += (CY(q) * CY(q) - 1.0f / 3.0f) * lq;
+        lPzz += (CZ(q) * CZ(q) - 1.0f / 3.0f) * lq;
+        lPxy += 2.0f * CX(q) * CY(q) * lq; lPyz += 2.0f * CY(q) * CZ(q) * lq; lPxz += 2.0f * CX(q) * CZ(q) * lq;
+    }
+    // Pi = sum c c fn - I tr/3: adjoint of fn_q (kept in f[])
+    const float ltr = -(lPxx + lPyy + lPzz) * (1.0f / 3.0f);
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+        f[q] = CX(q) * CX(q) * lPxx + CY(q) * CY(q) * lPyy + CZ(q) * CZ(q) * lPzz
+             + CX(q) * CY(q) * lPxy + CY(q) * CZ(q) * lPyz + CX(q) * CZ(q) * lPxz + ltr;
+    // unknown populations copied f^neq of the opposite one
+#pragma unroll
+    for (int q = 0; q < 19; ++q) if (CX(q) > 0) { f[18 - q] += f[q]; f[q] = 0.0f; }
+    // fn = fin - fe for the known ones; fe also enters out directly:
+    // lfe = lp - lfn, lfin = lfn
+    float lrin = 0.f, lvx = 0.f, lvy = 0.f, lvz = 0.f, lvv = 0.f;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const float lfe = lp[q] - f[q];
+        const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
+        lrin += WQ(q) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * vv) * lfe;
+        const float lcu = WQ(q) * rin * (3.0f + 9.0f * cu) * lfe;
+        lvx += CX(q) * lcu; lvy += CY(q) * lcu; lvz += CZ(q) * lcu;
+        lvv += -1.5f * WQ(q) * rin * lfe;
+    }
+    lvx += 2.0f * vx * lvv; lvy += 2.0f * vy * lvv; lvz += 2.0f * vz * lvv;
+    // rin = (1 + sk) / (1 - vx), sk = sum_{c_x=0} fin + 2 sum_{c_x<0} fin
+    const float ivx = rcp_approx(1.0f - vx);
+    const float lsk = lrin * ivx;
+    lvx += lrin * rin * ivx;
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+        lp[q] = CX(q) > 0 ? 0.0f : f[q] + (CX(q) == 0 ? lsk : 2.0f * lsk);
+    if (a.luin) {
+        float *o = a.luin + ((size_t)k * ny + j) * 3;
+        o[0] = lvx; o[1] = lvy; o[2] = lvz;
+    }
+}
+
 template <bool WALLBLOCK, bool SPONGE>
 __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int k, int tx, float (*sh)[4]) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -294,42 +387,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     // ---- inlet rebuild (eq:f_i, eq:bc_eq, eq:f_i_neq, eq:density_bc) ----
     const bool is_inlet = a.inlet && i == 0;
     float vx = 0.f, vy = 0.f, vz = 0.f, rin = 1.f;
-    if (is_inlet) {
-        const float *vp = a.vprime + ((size_t)k * ny + j) * 3;
-        const float *m = a.amat + 6 * j;
-        vx = a.UR[j] + m[0] * vp[0];
-        vy = m[1] * vp[0] + m[2] * vp[1];
-        vz = m[3] * vp[0] + m[4] * vp[1] + m[5] * vp[2];
-#pragma unroll
-        for (int q = 0; q < 19; ++q) f[q] -= WQ(q);
-        const float sk = (f[0] + f[2] + f[4] + f[6] + f[9] + f[12] + f[14] + f[16] + f[18])
-                       + 2.0f * (f[1] + f[5] + f[8] + f[11] + f[15]);
-        rin = (1.0f + sk) * rcp_approx(1.0f - vx);
-        const float drin = rin - 1.0f, vv = vx * vx + vy * vy + vz * vz;
-        auto feq = [&](int q) {
-            const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
-            return WQ(q) * (drin + rin * (3.0f * cu + 4.5f * cu * cu - 1.5f * vv));
-        };
-#pragma unroll
-        for (int q = 0; q < 19; ++q) if (CX(q) <= 0) f[q] -= feq(q);
-#pragma unroll
-        for (int q = 0; q < 19; ++q) if (CX(q) > 0) f[q] = f[18 - q];
-        float pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0, tr = 0;
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            pxx += CX(q) * CX(q) * f[q]; pyy += CY(q) * CY(q) * f[q]; pzz += CZ(q) * CZ(q) * f[q];
-            pxy += CX(q) * CY(q) * f[q]; pyz += CY(q) * CZ(q) * f[q]; pxz += CX(q) * CZ(q) * f[q];
-            tr += f[q];
-        }
-        pxx -= tr * (1.0f / 3.0f); pyy -= tr * (1.0f / 3.0f); pzz -= tr * (1.0f / 3.0f);
-        const float trp = (pxx + pyy + pzz) * (1.0f / 3.0f);
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const float qp = CX(q) * CX(q) * pxx + CY(q) * CY(q) * pyy + CZ(q) * CZ(q) * pzz
-                           + 2.0f * (CX(q) * CY(q) * pxy + CY(q) * CZ(q) * pyz + CX(q) * CZ(q) * pxz) - trp;
-            f[q] = feq(q) + 4.5f * WQ(q) * qp + WQ(q);
-        }
-    }
+    if (is_inlet) adjoint_inlet_forward(a, f, j, k, vx, vy, vz, rin);
     Pairs P;
     make_pairs<false>(f, P);
     const float f9 = f[9];
@@ -441,52 +499,7 @@ __device__ __forceinline__ void adjoint_cell(const AdjArgs &a, int i, int j, int
     adjoint_to_pops(lam, A, lp);
 
     // ---- reverse of the inlet rebuild ----
-    if (is_inlet) {
-        const float drin = rin - 1.0f, vv = vx * vx + vy * vy + vz * vz;
-        // out_q = fe_q + 4.5 w_q (c c : Pi - tr Pi / 3) + w_q
-        float lPxx = 0, lPyy = 0, lPzz = 0, lPxy = 0, lPyz = 0, lPxz = 0;
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const float lq = 4.5f * WQ(q) * lp[q];
-            lPxx += (CX(q) * CX(q) - 1.0f / 3.0f) * lq; lPyy += (CY(q) * CY(q) - 1.0f / 3.0f) * lq;
-            lPzz += (CZ(q) * CZ(q) - 1.0f / 3.0f) * lq;
-            lPxy += 2.0f * CX(q) * CY(q) * lq; lPyz += 2.0f * CY(q) * CZ(q) * lq; lPxz += 2.0f * CX(q) * CZ(q) * lq;
-        }
-        // Pi = sum c c fn - I tr/3: adjoint of fn_q (kept in f[])
-        const float ltr = -(lPxx + lPyy + lPzz) * (1.0f / 3.0f);
-#pragma unroll
-        for (int q = 0; q < 19; ++q)
-            f[q] = CX(q) * CX(q) * lPxx + CY(q) * CY(q) * lPyy + CZ(q) * CZ(q) * lPzz
-                 + CX(q) * CY(q) * lPxy + CY(q) * CZ(q) * lPyz + CX(q) * CZ(q) * lPxz + ltr;
-        // unknown populations copied f^neq of the opposite one
-#pragma unroll
-        for (int q = 0; q < 19; ++q) if (CX(q) > 0) { f[18 - q] += f[q]; f[q] = 0.0f; }
-        // fn = fin - fe for the known ones; fe also enters out directly:
-        // lfe = lp - lfn, lfin = lfn
-        float lrin = 0.f, lvx = 0.f, lvy = 0.f, lvz = 0.f, lvv = 0.f;
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const float lfe = lp[q] - f[q];
-            const float cu = CX(q) * vx + CY(q) * vy + CZ(q) * vz;
-            lrin += WQ(q) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * vv) * lfe;
-            const float lcu = WQ(q) * rin * (3.0f + 9.0f * cu) * lfe;
-            lvx += CX(q) * lcu; lvy += CY(q) * lcu; lvz += CZ(q) * lcu;
-            lvv += -1.5f * WQ(q) * rin * lfe;
-        }
-        (void)drin;
-        lvx += 2.0f * vx * lvv; lvy += 2.0f * vy * lvv; lvz += 2.0f * vz * lvv;
-        // rin = (1 + sk) / (1 - vx), sk = sum_{c_x=0} fin + 2 sum_{c_x<0} fin
-        const float ivx = rcp_approx(1.0f - vx);
-        const float lsk = lrin * ivx;
-        lvx += lrin * rin * ivx;
-#pragma unroll
-        for (int q = 0; q < 19; ++q)
-            lp[q] = CX(q) > 0 ? 0.0f : f[q] + (CX(q) == 0 ? lsk : 2.0f * lsk);
-        if (a.luin) {
-            float *o = a.luin + ((size_t)k * ny + j) * 3;
-            o[0] = lvx; o[1] = lvy; o[2] = lvz;
-        }
-    }
+    if (is_inlet) adjoint_inlet_reverse(a, f, lp, j, k, vx, vy, vz, rin);
 
     // ---- push the adjoint back to the pull sources ----
     // The outlet column's c_x < 0 entries are read twice in the forward step

@@ -180,6 +180,10 @@ struct lbm_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // a second side stream for the STG work of lbm_adjoint_step
     cudaStream_t aux = nullptr;
+    // lbm_adjoint_step: the recomputation of the next segment beside the
+    // reverse steps of the current one (its own stream; events per slot set)
+    cudaStream_t rstream = nullptr;
+    cudaEvent_t ev_rstart = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
     cudaEvent_t ev_aux_fork = nullptr, ev_aux_join = nullptr;
     // inlet profile uploads (lbm_set_inlet_profile): pinned staging of U_R and
     // amp chol(R), one half per device buffer, copied on their own stream;
@@ -441,7 +445,7 @@ struct lbm_handle {
         const size_t L = 19 * (size_t)ncell, W = 2 * (size_t)nz * nx, I = 3 * (size_t)nz * ny;
         const size_t N = n_modes > 0 ? n_modes : 1;
         adj.ckpt = ar.take<float>(L * (T / K));
-        adj.seg = ar.take<float>(L * (K - 1));
+        adj.seg = ar.take<float>(L * 2 * (K - 1));     // two sets of K - 1 segment slots
         adj.lamA = ar.take<float>(L);
         adj.lamB = ar.take<float>(L);
         adj.ut_init = ar.take<float>(W);
@@ -1892,10 +1896,12 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     // the states inside the last segment go straight to the segment slots,
     // so that the reverse sweep starts without recomputing them
     const int last_base = T - K;
+    // the K - 1 recomputed states of segment s sit in slot set s % 2
+    auto slots = [&](int sgm) { return A.seg + (size_t)(sgm % 2) * (K - 1) * L; };
     for (int n = 0; n < T; ++n) {
         void *out;
         if ((n + 1) % K == 0 && n + 1 < T) out = A.ckpt + (size_t)((n + 1) / K) * L;
-        else if (n + 1 > last_base && n + 1 < T) out = A.seg + (size_t)(n - last_base) * L;
+        else if (n + 1 > last_base && n + 1 < T) out = slots(T / K - 1) + (size_t)(n - last_base) * L;
         else { out = h->lat[pp]; pp ^= 1; }
         if (out == cur) { out = h->lat[pp]; pp ^= 1; }
         StepIO io;
@@ -1928,28 +1934,71 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     if ((e = cudaMemsetAsync(A.lamB, 0, L * 4, st)) != cudaSuccess) return cuda_fail(e);
     float *lam = A.lamA, *lout = A.lamB;
     const long long t_end = h->t;
-    for (int sgm = T / K - 1; sgm >= 0; --sgm) {
+    const int S = T / K;
+    // The recomputation of segment s - 1 is independent of the reverse steps
+    // of segment s: with one-launch adjoint steps (nx even) it runs on its own
+    // stream beside them, into the other slot set, once the reverse steps of
+    // segment s + 1 (which read that set) are done.  Same kernels, same inputs:
+    // the results do not depend on the overlap.
+    const bool overlap = h->nx % 2 == 0 && S > 1;
+    if (overlap) {
+        if (!h->rstream && (e = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e);
+        for (cudaEvent_t *ev : {&h->ev_rstart, &h->ev_rec[0], &h->ev_rec[1], &h->ev_rev[0], &h->ev_rev[1]})
+            if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e);
+        // the checkpoints, u_tau history and STG field of the forward pass are ready
+        if ((e = cudaEventRecord(h->ev_rstart, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->rstream, h->ev_rstart, 0)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    auto recompute = [&](int sgm, cudaStream_t on) -> cudaError_t {
         const int base = sgm * K;
         const float *prev = A.ckpt + (size_t)sgm * L;
-        // (the last segment's states are still in the slots from the forward pass)
-        for (int m = 1; m < K && sgm != T / K - 1; ++m) {
+        float *sl = slots(sgm);
+        const cudaStream_t keep = h->stream;
+        h->stream = on;
+        cudaError_t err = cudaSuccess;
+        for (int m = 1; m < K && err == cudaSuccess; ++m) {
             const int n = base + m - 1;
             StepIO io;
-            io.in = prev; io.out = A.seg + (size_t)(m - 1) * L;
+            io.in = prev; io.out = sl + (size_t)(m - 1) * L;
             io.utau_in = n == 0 ? A.ut_init : A.uthist + (size_t)(n - 1) * W;
             io.utau = A.ut_scr; io.fw = A.fw_scr; io.vprime = A.vwin + (size_t)n * I; io.stats = false;
             h->t = t0 + n;
-            if (cudaError_t le = launch_step_io(h, io)) return cuda_fail(le);
-            prev = A.seg + (size_t)(m - 1) * L;
+            err = launch_step_io(h, io);
+            prev = sl + (size_t)(m - 1) * L;
+        }
+        h->stream = keep;
+        return err;
+    };
+    for (int sgm = S - 1; sgm >= 0; --sgm) {
+        const int base = sgm * K;
+        // this segment's states: from the forward pass (the last one), from the
+        // recomputation enqueued beside the previous segment, or recomputed here
+        if (sgm != S - 1) {
+            if (overlap) {
+                if ((e = cudaStreamWaitEvent(st, h->ev_rec[sgm % 2], 0)) != cudaSuccess) return cuda_fail(e);
+            } else if (cudaError_t le = recompute(sgm, st)) {
+                return cuda_fail(le);
+            }
+        }
+        if (overlap && sgm >= 1) {
+            if (sgm + 1 <= S - 1 &&
+                (e = cudaStreamWaitEvent(h->rstream, h->ev_rev[(sgm + 1) % 2], 0)) != cudaSuccess)
+                return cuda_fail(e);
+            if (cudaError_t le = recompute(sgm - 1, h->rstream)) return cuda_fail(le);
+            if ((e = cudaEventRecord(h->ev_rec[(sgm - 1) % 2], h->rstream)) != cudaSuccess) return cuda_fail(e);
         }
         for (int n = base + K - 1; n >= base; --n) {
-            const float *sn = n == base ? A.ckpt + (size_t)sgm * L : A.seg + (size_t)(n - base - 1) * L;
+            const float *sn = n == base ? A.ckpt + (size_t)sgm * L : slots(sgm) + (size_t)(n - base - 1) * L;
             launch_adjoint(h, sn, lam, lout, A.uthist + (size_t)n * W, A.vwin + (size_t)n * I,
                            h->opts.inlet ? A.luin + (size_t)n * I : nullptr, true, obj, jtau_w);
             std::swap(lam, lout);
         }
+        if (overlap && (e = cudaEventRecord(h->ev_rev[sgm % 2], st)) != cudaSuccess) return cuda_fail(e);
         // theta gradient through this segment's inlet velocities, beside the
-        // next segment's recomputation
+        // next segment's reverse steps
         if (h->opts.inlet) {
             if ((e = cudaEventRecord(h->ev_aux_fork, st)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(h->aux, h->ev_aux_fork, 0)) != cudaSuccess)
@@ -2254,6 +2303,9 @@ void lbm_destroy(lbm_handle *h) {
     if (h->ev_stg_ready) cudaEventDestroy(h->ev_stg_ready);
     if (h->ev_shear) cudaEventDestroy(h->ev_shear);
     graphs_clear(h);
+    if (h->rstream) { cudaStreamSynchronize(h->rstream); cudaStreamDestroy(h->rstream); }
+    for (cudaEvent_t ev : {h->ev_rstart, h->ev_rec[0], h->ev_rec[1], h->ev_rev[0], h->ev_rev[1]})
+        if (ev) cudaEventDestroy(ev);
     if (h->ev_gfork) cudaEventDestroy(h->ev_gfork);
     if (h->ev_gjoin) cudaEventDestroy(h->ev_gjoin);
     if (h->gstream) cudaStreamDestroy(h->gstream);
