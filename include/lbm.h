@@ -425,10 +425,12 @@ int lbm_adjoint_bind(lbm_handle *h, int window, int ckpt_every, void *dev_ptr, s
 
 /* Advance the state `window` steps (exactly as lbm_step would), evaluate J over
  * them and its gradient by the hand-written adjoint of the fused step: store
- * s_0 and every ckpt_every-th state, then for each segment in reverse
- * recompute its states from the checkpoint and run the adjoint steps
- * backwards (for even nx, a segment's recomputation runs on a stream of the
- * handle beside the reverse steps of the segment after it).  *J and dJ_dtheta[4] are host FP64.  dJ/ds_0 is kept for
+ * s_0 and every ckpt_every-th state (and all states of the last two
+ * segments, in the two sets of segment lattices), then for each segment in
+ * reverse recompute its states from the checkpoint (except the last two) and
+ * run the adjoint steps backwards (for even nx, a segment's recomputation
+ * runs on a stream of the handle beside the reverse steps of the segment
+ * after it).  *J and dJ_dtheta[4] are host FP64.  dJ/ds_0 is kept for
  * lbm_adjoint_state_gradient.  Synchronizes.  Errors: LBM_EINVAL for a
  * window or objective range the workspace or the grid does not fit, the
  * common ones otherwise (binds a workspace first if none is bound). */

@@ -573,15 +573,26 @@ __device__ __forceinline__ V2 vsel(bool a, bool b, V2 v) {   // per-lane keep or
     return make_float2(a ? v.x : 0.0f, b ? v.y : 0.0f);
 }
 
-// Reverse of the force-free collision of two cells.  lam: dJ/df* of the two
-// cells; (lux, luy): direct dJ/du seeds.  Returns the adjoint of the pulled
-// populations in lp (the identity part lam included).
-__device__ __forceinline__ void collide_adjoint2(const V2 (&lam)[19], const Pairs2 &P, V2 tau0, float csm18,
-                                                 V2 lux, V2 luy, V2 (&lp)[19]) {
+// Adjoint of the collision inputs of two cells (the packed AdjIn).
+struct AdjIn2 {
+    V2 ls[9], ld[9];        // of the pair sums / differences
+    V2 lf9, lrho;           // of f_9 and rho
+    V2 ljx, ljy, ljz;       // of the momentum sum f c (before the force)
+    V2 lFx, lFz;            // of the wall force (F_y = 0: the force is wall-parallel)
+};
+
+// Reverse of collide_pairs2<false, HAS_FORCE> for two cells: lam = dJ/df*;
+// (lux, luy) direct dJ/du seeds; (Fx, 0, Fz) the wall force when HAS_FORCE.
+// A receives the adjoint of the collision's inputs (the identity part lam is
+// added by adjoint_to_pops2).
+template <bool HAS_FORCE>
+__device__ __forceinline__ void collide_adjoint2(const V2 (&lam)[19], const Pairs2 &P, V2 Fx, V2 Fz, V2 tau0,
+                                                 float csm18, V2 lux, V2 luy, AdjIn2 &A) {
     const V2 *s = P.s;
     // ---- forward values ----
     const V2 rho = P.rho, irho = vrcp(rho);
-    const V2 rux = P.jx, ruy = P.jy, ruz = P.jz;
+    const V2 rux = HAS_FORCE ? vfma(0.5f, Fx, P.jx) : P.jx, ruy = P.jy;
+    const V2 ruz = HAS_FORCE ? vfma(0.5f, Fz, P.jz) : P.jz;
     const V2 ux = rux * irho, uy = ruy * irho, uz = ruz * irho;
     const V2 uxx = rux * ux, uyy = ruy * uy, uzz = ruz * uz;
     const V2 usq = (uxx + uyy) + uzz;
@@ -602,6 +613,13 @@ __device__ __forceinline__ void collide_adjoint2(const V2 (&lam)[19], const Pair
     const V2 Qh = vsqrt(qq);
     const V2 Rr = vsqrt(vfma(csm18 * Qh, irho, tau0 * tau0));
     const V2 sv = 2.0f * vrcp(tau0 + Rr);
+    // Guo source moments with F_y = 0 (collide_pairs2)
+    V2 F9 = vdup(0.0f), F11 = vdup(0.0f), F13 = vdup(0.0f), F14 = vdup(0.0f), F15 = vdup(0.0f);
+    if (HAS_FORCE) {
+        F9 = vfma(4.0f, ux * Fx, -2.0f * (uz * Fz));
+        F11 = -2.0f * (uz * Fz);
+        F13 = uy * Fx; F14 = uy * Fz; F15 = vfma(ux, Fz, uz * Fx);
+    }
     // ---- mu = M lambda ----
     V2 ls[9], ld[9];
 #pragma unroll
@@ -635,9 +653,33 @@ __device__ __forceinline__ void collide_adjoint2(const V2 (&lam)[19], const Pair
     const V2 sv4 = msv * 0.25f;
     V2 bn13 = m13 * sv4, bn14 = m14 * sv4, bn15 = m15 * sv4;
     const V2 bn16 = m16 * (-S_M * 0.125f), bn17 = m17 * (-S_M * 0.125f), bn18 = m18 * (-S_M * 0.125f);
-    const V2 bsv = vfma(m9 * n9, vdup(-1.0f / 36.0f),
-                        vfma(m11 * n11, vdup(-1.0f / 12.0f),
-                             (vfma(m13, n13, vfma(m14, n14, m15 * n15))) * -0.25f));
+    // d/dsv of (sv n - (1 - sv/2) F) = n + F/2
+    const V2 bsv = HAS_FORCE
+        ? vfma(m9 * vfma(0.5f, F9, n9), vdup(-1.0f / 36.0f),
+               vfma(m11 * vfma(0.5f, F11, n11), vdup(-1.0f / 12.0f),
+                    (vfma(m13, vfma(0.5f, F13, n13), vfma(m14, vfma(0.5f, F14, n14), m15 * vfma(0.5f, F15, n15)))) *
+                        -0.25f))
+        : vfma(m9 * n9, vdup(-1.0f / 36.0f),
+               vfma(m11 * n11, vdup(-1.0f / 12.0f), (vfma(m13, n13, vfma(m14, n14, m15 * n15))) * -0.25f));
+    V2 lux_ = lux, luy_ = luy, luz_ = vdup(0.0f), lFx = vdup(0.0f), lFz = vdup(0.0f);
+    if (HAS_FORCE) {
+        const V2 m3 = DX - ld[8], m7 = DZ - ld[2];
+        const V2 hv = vfma(-0.5f, sv, vdup(1.0f));
+        const float cq = (1.0f - 0.5f * S_Q) * (2.0f / 3.0f) * (1.0f / 40.0f);
+        const V2 buF = vfma(-(1.0f - 0.5f * S_EPS) * 11.0f / 252.0f, m2, m1 * ((1.0f - 0.5f * S_E) * 38.0f / 2394.0f));
+        lFx = vfma(0.1f, m3, m4 * -cq);
+        lFz = vfma(0.1f, m7, m8 * -cq);
+        const V2 bF9 = vfma(m9 * (1.0f / 36.0f), hv, m10 * (-(1.0f - 0.5f * S_PI) * 0.5f / 72.0f));
+        const V2 bF11 = vfma(m11 * (1.0f / 12.0f), hv, m12 * (-(1.0f - 0.5f * S_PI) * 0.5f / 24.0f));
+        const V2 bF13 = m13 * hv * 0.25f, bF14 = m14 * hv * 0.25f, bF15 = m15 * hv * 0.25f;
+        // uF = ux Fx + uz Fz; F9 = 4 ux Fx - 2 uz Fz; F11 = -2 uz Fz;
+        // F13 = uy Fx; F14 = uy Fz; F15 = ux Fz + uz Fx
+        lux_ = vfma(Fx, buF + 4.0f * bF9, vfma(Fz, bF15, lux_));
+        luy_ = vfma(Fx, bF13, vfma(Fz, bF14, luy_));
+        luz_ = vfma(Fz, buF - 2.0f * (bF9 + bF11), Fx * bF15);
+        lFx = vfma(ux, buF + 4.0f * bF9, vfma(uy, bF13, vfma(uz, bF15, lFx)));
+        lFz = vfma(uz, buF - 2.0f * (bF9 + bF11), vfma(uy, bF14, vfma(ux, bF15, lFz)));
+    }
     // ---- SGS: sv = 2 / (tau0 + sqrt(tau0^2 + c Qh / rho)) ----
     const V2 lX = bsv * (-0.25f) * sv * sv * vrcp(Rr);
     const V2 lQh = lX * irho * csm18;
@@ -654,143 +696,341 @@ __device__ __forceinline__ void collide_adjoint2(const V2 (&lam)[19], const Pair
     // ---- n_k -> pair sums / differences, rho, rho u ----
     V2 lrho = vfma(11.0f, bn1, -3.0f * bn2);
     const V2 lusq = vfma(-19.0f, bn1, 5.5f * bn2);
-    const V2 lf9 = vfma(-30.0f, bn1, 12.0f * bn2);
+    A.lf9 = vfma(-30.0f, bn1, 12.0f * bn2);
     const V2 lSax = vfma(-11.0f, bn1, -4.0f * bn2), lSdg = vfma(8.0f, bn1, bn2);
     const V2 b910 = bn9 + bn10, b1112 = bn11 + bn12;
-    V2 las[9], lad[9];
-    las[0] = (lSdg - 2.0f * b910) + bn14;
-    las[4] = (lSdg - 2.0f * b910) - bn14;
-    las[1] = ((lSdg + b910) - b1112) + bn15;
-    las[3] = ((lSdg + b910) - b1112) - bn15;
-    las[5] = ((lSdg + b910) + b1112) + bn13;
-    las[7] = ((lSdg + b910) + b1112) - bn13;
-    las[2] = vfma(2.0f, bn10 + bn12, lSax - (bn9 + bn11));
-    las[6] = vfma(2.0f, bn10 - bn12, (lSax - bn9) + bn11);
-    las[8] = vfma(2.0f, bn9, vfma(-4.0f, bn10, lSax));
-    lad[1] = bn16 - bn18; lad[3] = -(bn16 + bn18);
-    lad[7] = bn16 + bn17; lad[5] = bn17 - bn16;
-    lad[4] = bn17 + bn18; lad[0] = bn18 - bn17;
-    lad[8] = 5.0f * bn4; lad[6] = 5.0f * bn6; lad[2] = 5.0f * bn8;
+    A.ls[0] = (lSdg - 2.0f * b910) + bn14;
+    A.ls[4] = (lSdg - 2.0f * b910) - bn14;
+    A.ls[1] = ((lSdg + b910) - b1112) + bn15;
+    A.ls[3] = ((lSdg + b910) - b1112) - bn15;
+    A.ls[5] = ((lSdg + b910) + b1112) + bn13;
+    A.ls[7] = ((lSdg + b910) + b1112) - bn13;
+    A.ls[2] = vfma(2.0f, bn10 + bn12, lSax - (bn9 + bn11));
+    A.ls[6] = vfma(2.0f, bn10 - bn12, (lSax - bn9) + bn11);
+    A.ls[8] = vfma(2.0f, bn9, vfma(-4.0f, bn10, lSax));
+    A.ld[1] = bn16 - bn18; A.ld[3] = -(bn16 + bn18);
+    A.ld[7] = bn16 + bn17; A.ld[5] = bn17 - bn16;
+    A.ld[4] = bn17 + bn18; A.ld[0] = bn18 - bn17;
+    A.ld[8] = 5.0f * bn4; A.ld[6] = 5.0f * bn6; A.ld[2] = 5.0f * bn8;
     const V2 lpxxeq = vfma(0.5f, bn10, -bn9), lpwweq = vfma(0.5f, bn12, -bn11);
     const V2 luxx = vfma(2.0f, lpxxeq, lusq), luyy = (lusq - lpxxeq) + lpwweq, luzz = (lusq - lpxxeq) - lpwweq;
     // uxx = rux ux, uyy = ruy uy, uzz = ruz uz, uxy = rux uy, uyz = ruy uz, uxz = rux uz
     // with a_uxy = -bn13, a_uyz = -bn14, a_uxz = -bn15; u = ru / rho
-    const V2 lux_ = vfma(rux, luxx, lux);
-    const V2 luy_ = vfma(ruy, luyy, luy) - rux * bn13;
-    const V2 luz_ = vfma(ruz, luzz, -(ruy * bn14 + rux * bn15));
+    lux_ = vfma(rux, luxx, lux_);
+    luy_ = vfma(ruy, luyy, luy_) - rux * bn13;
+    luz_ = vfma(ruz, luzz, luz_) - (ruy * bn14 + rux * bn15);
     V2 lrux = vfma(2.0f / 3.0f, bn4, vfma(ux, luxx, -(uy * bn13 + uz * bn15)));
     V2 lruy = vfma(2.0f / 3.0f, bn6, vfma(uy, luyy, -(uz * bn14)));
     V2 lruz = vfma(2.0f / 3.0f, bn8, uz * luzz);
     lrux = vfma(irho, lux_, lrux); lruy = vfma(irho, luy_, lruy); lruz = vfma(irho, luz_, lruz);
     lirho = lirho + vfma(rux, lux_, vfma(ruy, luy_, ruz * luz_));
-    lrho = lrho - irho * irho * lirho;
-    // j = momentum sum: n4 = jx + ..., so a_jx = bn4 + a_rux (rux = jx here)
-    const V2 ljx = bn4 + lrux, ljy = bn6 + lruy, ljz = bn8 + lruz;
-    // ---- to the populations: rho = sum f, j from the differences ----
-    lad[3] = lad[3] + ljx - ljz; lad[1] = lad[1] - ljx - ljz; lad[7] = lad[7] + ljx - ljy; lad[5] = lad[5] - ljx - ljy;
-    lad[8] = lad[8] - ljx;
-    lad[4] = lad[4] + ljy - ljz; lad[0] = lad[0] - ljy - ljz; lad[6] = lad[6] - ljy;
-    lad[2] = lad[2] - ljz;
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        const V2 a = las[p] + lrho;
-        lp[p] = (lam[p] + a) + lad[p];
-        lp[18 - p] = (lam[18 - p] + a) - lad[p];
-    }
-    lp[9] = (lam[9] + lf9) + lrho;
+    A.lrho = lrho - irho * irho * lirho;
+    // n4 = jx + 5 d8 + 2/3 rux and ru = j + F/2
+    A.ljx = bn4 + lrux; A.ljy = bn6 + lruy; A.ljz = bn8 + lruz;
+    A.lFx = HAS_FORCE ? vfma(0.5f, lrux, lFx) : lFx;
+    A.lFz = HAS_FORCE ? vfma(0.5f, lruz, lFz) : lFz;
 }
 
-template <bool SPONGE>
-__device__ __forceinline__ void adjoint_pair(const AdjArgs &a, int i0, int j, int k) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long N = (long long)nx * ny * nz;
-    // pull geometry (interior row, no wall mirror); x wraps when the inlet is off
-    int xm0 = i0 - 1, xp1 = i0 + 2;
-    if (!a.inlet) { xm0 = xm0 < 0 ? nx - 1 : xm0; xp1 = xp1 >= nx ? 0 : xp1; }
-    const int plane = nx * ny;
-    const int ozm = k == 0 ? (nz - 1) * plane : -plane;
-    const int ozp = k == nz - 1 ? -(nz - 1) * plane : plane;
-    const int o00 = (k * ny + j) * nx;
-    auto row = [&](int q) {
-        return o00 + (CY(q) < 0 ? nx : (CY(q) > 0 ? -nx : 0)) + (CZ(q) < 0 ? ozp : (CZ(q) > 0 ? ozm : 0));
-    };
-    V2 f[19];
+// The adjoint of the pulled populations of two cells from that of the
+// collision inputs: rho = sum f, j from the differences, s / d the pairs.
+__device__ __forceinline__ void adjoint_to_pops2(const V2 (&lam)[19], const AdjIn2 &A, V2 (&lp)[19]) {
+    V2 ld[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) ld[p] = A.ld[p];
+    ld[3] = ld[3] + A.ljx - A.ljz; ld[1] = ld[1] - A.ljx - A.ljz; ld[7] = ld[7] + A.ljx - A.ljy;
+    ld[5] = ld[5] - A.ljx - A.ljy; ld[8] = ld[8] - A.ljx;
+    ld[4] = ld[4] + A.ljy - A.ljz; ld[0] = ld[0] - A.ljy - A.ljz; ld[6] = ld[6] - A.ljy;
+    ld[2] = ld[2] - A.ljz;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const V2 a = A.ls[p] + A.lrho;
+        lp[p] = (lam[p] + a) + ld[p];
+        lp[18 - p] = (lam[18 - p] + a) - ld[p];
+    }
+    lp[9] = (lam[9] + A.lf9) + A.lrho;
+}
+
+// Pull geometry of two x-adjacent cells (i0, i0 + 1) of row j, plane k: the
+// source plane of population q (mirrored through a slip wall) and the row /
+// plane offset of its source; x sources xm0 (the lo cell's c_x = +1) and xp1
+// (the hi cell's c_x = -1), wrapped when the inlet is off.
+struct PairGeom {
+    int o00, ozm, ozp, xm0, xp1, nx;
+    bool bot, top;
+    __device__ __forceinline__ int plane(int q) const {
+        return ((CY(q) > 0 && bot) || (CY(q) < 0 && top)) ? mirror_y(q) : q;
+    }
+    __device__ __forceinline__ int row(int q) const {
+        const bool mir = (CY(q) > 0 && bot) || (CY(q) < 0 && top);
+        return o00 + (mir ? 0 : (CY(q) < 0 ? nx : (CY(q) > 0 ? -nx : 0))) +
+               (CZ(q) < 0 ? ozp : (CZ(q) > 0 ? ozm : 0));
+    }
+};
+__device__ __forceinline__ PairGeom pair_geom(const AdjArgs &a, int i0, int j, int k) {
+    PairGeom g;
+    g.nx = a.nx;
+    g.xm0 = i0 - 1; g.xp1 = i0 + 2;
+    if (!a.inlet) { g.xm0 = g.xm0 < 0 ? a.nx - 1 : g.xm0; g.xp1 = g.xp1 >= a.nx ? 0 : g.xp1; }
+    const int plane = a.nx * a.ny;
+    g.ozm = k == 0 ? (a.nz - 1) * plane : -plane;
+    g.ozp = k == a.nz - 1 ? -(a.nz - 1) * plane : plane;
+    g.o00 = (k * a.ny + j) * a.nx;
+    g.bot = j == 0; g.top = j == a.ny - 1;
+    return g;
+}
+__device__ __forceinline__ void pull_pair(const AdjArgs &a, const PairGeom &g, int i0, V2 (&f)[19]) {
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
-        const float *r = a.in[q] + row(q);
+        const float *r = a.in[g.plane(q)] + g.row(q);
         if (CX(q) == 0) f[q] = *reinterpret_cast<const float2 *>(r + i0);
-        else if (CX(q) > 0) f[q] = make_float2(r[xm0], r[i0]);
-        else f[q] = make_float2(r[i0 + 1], r[xp1]);
+        else if (CX(q) > 0) f[q] = make_float2(r[g.xm0], r[i0]);
+        else f[q] = make_float2(r[i0 + 1], r[g.xp1]);
     }
-    V2 lam[19];
-    const int c = o00 + i0;
+}
+__device__ __forceinline__ void push_pair(const AdjArgs &a, const PairGeom &g, int i0, const V2 (&lp)[19]) {
+    const long long N = (long long)a.nx * a.ny * a.nz;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        float *r = a.lout + g.plane(q) * N + g.row(q);
+        if (CX(q) == 0) *reinterpret_cast<float2 *>(r + i0) = lp[q];
+        else if (CX(q) > 0) { r[g.xm0] = lp[q].x; r[i0] = lp[q].y; }
+        else { r[i0 + 1] = lp[q].x; r[g.xp1] = lp[q].y; }
+    }
+}
+// J_R seeds (dJ_R/du, dJ_R/dv) of the two cells when one of them sits at x = i_R
+__device__ __forceinline__ void jr_seeds2(const AdjArgs &a, const Pairs2 &P, V2 Fx, int i0, int j, V2 &lux,
+                                          V2 &luy) {
+    lux = luy = vdup(0.0f);
+    if (a.jr_coef && (i0 == a.i_R || i0 + 1 == a.i_R)) {
+        const V2 ir = vrcp(P.rho);
+        const V2 uu = vfma(0.5f, Fx, P.jx) * ir, vv = P.jy * ir;
+        const float cj = a.jr_coef[j];
+        const bool lo = i0 == a.i_R;
+        lux = vsel(lo, !lo, cj * (vv - vdup(a.jr_mean[a.ny + j])));
+        luy = vsel(lo, !lo, cj * (uu - vdup(a.jr_mean[j])));
+    }
+}
+template <bool SPONGE>
+__device__ __forceinline__ V2 pair_tau0_adj(const AdjArgs &a, int i0) {
+    return SPONGE ? make_float2(sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, i0),
+                                sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, i0 + 1))
+                  : vdup(a.tau0);
+}
+
+// Interior rows 2 .. ny-3, two cells per thread (neither the inlet cell nor
+// one whose populations the outlet's clamped pull shares).
+template <bool SPONGE>
+__device__ __forceinline__ void adjoint_pair(const AdjArgs &a, int i0, int j, int k) {
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    const PairGeom g = pair_geom(a, i0, j, k);
+    V2 f[19], lam[19];
+    pull_pair(a, g, i0, f);
+    const int c = g.o00 + i0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) lam[q] = *reinterpret_cast<const float2 *>(a.lam + q * N + c);
     Pairs2 P;
     make_pairs2<false>(f, P);
-    V2 lux = vdup(0.0f), luy = vdup(0.0f);
-    if (a.jr_coef && (i0 == a.i_R || i0 + 1 == a.i_R)) {
-        // J_R: d/du of the <u'v'> terms, u and v of this collision
-        const V2 ir = vrcp(P.rho);
-        const V2 uu = P.jx * ir, vv = P.jy * ir;
-        const float cj = a.jr_coef[j];
-        const bool lo = i0 == a.i_R;
-        lux = vsel(lo, !lo, cj * (vv - vdup(a.jr_mean[ny + j])));
-        luy = vsel(lo, !lo, cj * (uu - vdup(a.jr_mean[j])));
-    }
-    const V2 t0c = SPONGE ? make_float2(sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, i0),
-                                        sponge_tau0(a.tau0, a.sp_x0, a.sp_inv, a.sp_3nu, i0 + 1))
-                          : vdup(a.tau0);
+    V2 lux, luy;
+    jr_seeds2(a, P, vdup(0.0f), i0, j, lux, luy);
+    AdjIn2 A;
+    collide_adjoint2<false>(lam, P, vdup(0.0f), vdup(0.0f), pair_tau0_adj<SPONGE>(a, i0), a.csm18, lux, luy, A);
     V2 lp[19];
-    collide_adjoint2(lam, P, t0c, a.csm18, lux, luy, lp);
-    // push to the pull sources (a permutation for these cells)
+    adjoint_to_pops2(lam, A, lp);
+    push_pair(a, g, i0, lp);
+}
+
+// A wall row and its second row, two x-adjacent cells per thread: the
+// threads of row ty = 0 and ty = 1 of the block hold the wall row and the
+// second row (bottom: 0 and 1; top: ny-2 and ny-1) at the same x, and trade
+// u_2 (forward) and its adjoint through sh[slot], slot = the cell's x within
+// the block.  `active`: a pair away from the inlet and the outlet's shared
+// reads (the others take the one-cell path); every thread reaches the two
+// barriers, inactive ones on in-bounds placeholder cells whose results are
+// dropped.  The reverse of the wall model (Sec. 2.3) runs per lane as in
+// adjoint_cell: u_tau through the implicit function theorem, then e_x and u_2.
+template <bool SPONGE>
+__device__ __forceinline__ void adjoint_wall_pair(const AdjArgs &a, int i0, int j, int k, bool active, int slot,
+                                                  float (*sh)[4]) {
+    const int nx = a.nx, nz = a.nz;
+    const long long N = (long long)nx * a.ny * nz;
+    const int ic = active ? i0 : 2;
+    const PairGeom g = pair_geom(a, ic, j, k);
+    const bool is_wall = g.bot || g.top;                  // warp-uniform (one row per warp)
+    V2 f[19], lam[19];
+    pull_pair(a, g, ic, f);
+    const int c = g.o00 + ic;
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        float *r = a.lout + q * N + row(q);
-        if (CX(q) == 0) *reinterpret_cast<float2 *>(r + i0) = lp[q];
-        else if (CX(q) > 0) { r[xm0] = lp[q].x; r[i0] = lp[q].y; }
-        else { r[i0 + 1] = lp[q].x; r[xp1] = lp[q].y; }
+    for (int q = 0; q < 19; ++q) lam[q] = *reinterpret_cast<const float2 *>(a.lam + q * N + c);
+    Pairs2 P;
+    make_pairs2<false>(f, P);
+    // ---- wall model forward (eq:base, eq:uhat, this step's u_tau, eq:force_wm) ----
+    // Per lane from u_2 (in sh), the cell's momentum and density and this
+    // step's u_tau; evaluated for the force here and again in the reverse
+    // below, so that no per-lane state lives across the collision's reverse.
+    const int w = g.bot ? 0 : 1;
+    struct WallLane { float ex, ez, tn, ut, sg, j2x, j2z, ir2; };
+    auto wall_lane = [&](int l) {
+        WallLane v{0.f, 0.f, 0.f, 0.f, 1.f, sh[slot + l][0], sh[slot + l][1], sh[slot + l][2]};
+        const float u2x = v.j2x * v.ir2, u2z = v.j2z * v.ir2;
+        v.tn = sqrt_approx(u2x * u2x + u2z * u2z);
+        if (v.tn >= 1e-12f) {
+            const float itn = rcp_approx(v.tn);
+            v.ex = u2x * itn; v.ez = u2z * itn;
+            const float jx = l ? P.jx.y : P.jx.x, jz = l ? P.jz.y : P.jz.x, rw = l ? P.rho.y : P.rho.x;
+            const float uhat = (jx * v.ex + jz * v.ez) * rcp_approx(rw);
+            v.sg = uhat < 0.0f ? -1.0f : 1.0f;
+            // the forward step stored this step's solution of eq:u_tau_implicit
+            if (fabsf(uhat) > 0.0f && active) v.ut = a.utau[((size_t)w * nz + k) * nx + ic + l];
+        }
+        return v;
+    };
+    V2 Fx = vdup(0.0f), Fz = vdup(0.0f);
+    if (a.wall_model) {
+        if (!is_wall) {
+            const V2 ir = vrcp(P.rho);
+            sh[slot][0] = P.jx.x; sh[slot][1] = P.jz.x; sh[slot][2] = ir.x;
+            sh[slot + 1][0] = P.jx.y; sh[slot + 1][1] = P.jz.y; sh[slot + 1][2] = ir.y;
+        }
+        __syncthreads();
+        if (is_wall) {
+            const WallLane v0 = wall_lane(0), v1 = wall_lane(1);
+            const float tw0 = P.rho.x * v0.ut * v0.ut * v0.sg, tw1 = P.rho.y * v1.ut * v1.ut * v1.sg;
+            Fx = make_float2(-tw0 * v0.ex, -tw1 * v1.ex);
+            Fz = make_float2(-tw0 * v0.ez, -tw1 * v1.ez);
+        }
+        __syncthreads();                          // the second rows' slots stay as they are until
+                                                  // the wall rows' reverse below has read them
     }
+    // ---- reverse of the collision (with the objective seeds) ----
+    V2 lux, luy;
+    jr_seeds2(a, P, Fx, ic, j, lux, luy);
+    AdjIn2 A;
+    const V2 t0c = pair_tau0_adj<SPONGE>(a, ic);
+    if (is_wall && a.wall_model) collide_adjoint2<true>(lam, P, Fx, Fz, t0c, a.csm18, lux, luy, A);
+    else collide_adjoint2<false>(lam, P, Fx, Fz, t0c, a.csm18, lux, luy, A);
+    // ---- reverse of the wall model ----
+    if (a.wall_model) {
+        float gk = 0.f, gB = 0.f;
+        if (is_wall) {
+            const float lFx[2] = {A.lFx.x, A.lFx.y}, lFz[2] = {A.lFz.x, A.lFz.y};
+            const float rw[2] = {P.rho.x, P.rho.y}, jxw[2] = {P.jx.x, P.jx.y}, jzw[2] = {P.jz.x, P.jz.y};
+            const WallLane vl[2] = {wall_lane(0), wall_lane(1)};
+            float dljx[2] = {0.f, 0.f}, dljz[2] = {0.f, 0.f}, dlrho[2] = {0.f, 0.f};
+            float lj2x[2] = {0.f, 0.f}, lj2z[2] = {0.f, 0.f}, li2[2] = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const WallLane &v = vl[l];
+                if (!(v.tn >= 1e-12f && active)) continue;
+                const float tw = rw[l] * v.ut * v.ut * v.sg;
+                const float ltw = -(lFx[l] * v.ex + lFz[l] * v.ez);
+                float lex = -tw * lFx[l], lez = -tw * lFz[l];
+                // tau = rho ut^2 (unsigned), tw = tau sg; J_tau weight on tau
+                float ltau = v.sg * ltw;
+                if (ic + l >= a.i_tau0 && ic + l < a.i_tau1) ltau += a.jtau_w;
+                dlrho[l] += v.ut * v.ut * ltau;
+                const float lut = 2.0f * rw[l] * v.ut * ltau;
+                if (v.ut > 0.0f) {
+                    float up, dup, dk, dB;
+                    const float yp = a.y1_nu * v.ut;
+                    reichardt_partials(yp, a.kappa, a.B, up, dup, dk, dB);
+                    const float iRu = rcp_approx(up + yp * dup);
+                    gk -= lut * v.ut * dk * iRu;
+                    gB -= lut * v.ut * dB * iRu;
+                    const float luh = v.sg * lut * iRu;
+                    const float irw = rcp_approx(rw[l]);
+                    // uhat = (jx ex + jz ez) / rho_w
+                    dljx[l] += v.ex * irw * luh; dljz[l] += v.ez * irw * luh;
+                    lex += jxw[l] * irw * luh; lez += jzw[l] * irw * luh;
+                    dlrho[l] -= irw * irw * (jxw[l] * v.ex + jzw[l] * v.ez) * luh;
+                }
+                // e = t / |t|, t = (u2x, u2z); u2 = j2 / rho2
+                const float dot = lex * v.ex + lez * v.ez;
+                const float itn = rcp_approx(v.tn);
+                const float lu2x = (lex - dot * v.ex) * itn, lu2z = (lez - dot * v.ez) * itn;
+                lj2x[l] = v.ir2 * lu2x; lj2z[l] = v.ir2 * lu2z;
+                li2[l] = v.j2x * lu2x + v.j2z * lu2z;
+            }
+            A.ljx = A.ljx + make_float2(dljx[0], dljx[1]);
+            A.ljz = A.ljz + make_float2(dljz[0], dljz[1]);
+            A.lrho = A.lrho + make_float2(dlrho[0], dlrho[1]);
+#pragma unroll
+            for (int l = 0; l < 2; ++l) { sh[slot + l][0] = lj2x[l]; sh[slot + l][1] = lj2z[l]; sh[slot + l][2] = li2[l]; }
+        }
+        __syncthreads();
+        if (!is_wall) {
+            const V2 ir = vrcp(P.rho);
+            A.ljx = A.ljx + make_float2(sh[slot][0], sh[slot + 1][0]);
+            A.ljz = A.ljz + make_float2(sh[slot][1], sh[slot + 1][1]);
+            A.lrho = A.lrho - ir * ir * make_float2(sh[slot][2], sh[slot + 1][2]);
+        }
+        // theta gradient of the wall model: warp reduction, one atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gk += __shfl_xor_sync(0xffffffffu, gk, o);
+            gB += __shfl_xor_sync(0xffffffffu, gB, o);
+        }
+        if ((threadIdx.x & 31) == 0 && (gk != 0.f || gB != 0.f)) {
+            atomicAdd(a.gtheta + 2, (double)gk);
+            atomicAdd(a.gtheta + 3, (double)gB);
+        }
+    }
+    if (!active) return;
+    V2 lp[19];
+    adjoint_to_pops2(lam, A, lp);
+    push_pair(a, g, ic, lp);
 }
 
 #ifndef LBM_ADJ2_MINB
 #define LBM_ADJ2_MINB 4
 #endif
 
-// One reverse step in one launch (nx even): blocks [0, nw) do the wall rows
-// and their second rows as adjoint_wall_kernel does, blocks [nw, nw + ne) the
-// inlet and outlet columns of rows 2..ny-3 one cell per thread, and the rest
-// the packed interior pairs.  Blocks start in index order, so the long
-// per-cell chains of the first two parts run beside the interior pairs
-// instead of after them.  Block (64, BY); the parts write disjoint entries
-// (the outlet's shared entries take atomics).
+// One reverse step in one launch (nx even, block (64, BY)), in this order of
+// blocks: [0, nwp) the wall rows and their second rows two cells per thread
+// (adjoint_wall_pair; ty = 0, 1 the two rows, 128 x cells per block); with the
+// inlet on, [nwp, nwp + nwe) the same rows at x = 0, 1, nx-2, nx-1 one cell per
+// thread (adjoint_cell, tx = column + 4 x plane within 16 planes), and
+// [.., + ne) those columns of rows 2..ny-3; the rest the other cells of rows
+// 2..ny-3 two per thread.  Blocks start in index order, so the longer chains of
+// the first parts run beside the interior pairs.  The parts write disjoint
+// entries (the outlet's shared entries take atomics).
 template <bool SPONGE>
 __global__ void __launch_bounds__(128, LBM_ADJ2_MINB)
-    adjoint_fused_kernel(const __grid_constant__ AdjArgs a, int nw, int ne) {
-    __shared__ float sh[128 / BY][4];
+    adjoint_fused_kernel(const __grid_constant__ AdjArgs a, int nwp, int nwe, int ne) {
+    __shared__ float sh[128][4];
     const int b = blockIdx.x;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    if (b < nw) {                                    // rows 0, 1 and ny-2, ny-1
-        const int nbx = (a.nx + 63) / 64;
+    const int nx = a.nx;
+    if (b < nwp) {                                   // wall rows, two cells per thread
+        const int nbx = (nx + 127) / 128;
         const int bx = b % nbx, r = b / nbx;
         const int j = (r % 2) == 0 ? ty : a.ny - 2 + ty;
-        adjoint_cell<true, SPONGE>(a, bx * 64 + tx, j, r / 2, tx, sh);
+        const int i0 = 2 * (bx * 64 + tx);
+        const bool active = i0 < nx && (!a.inlet || (i0 >= 2 && i0 + 2 < nx));
+        adjoint_wall_pair<SPONGE>(a, i0, j, r / 2, active, 2 * tx, sh);
         return;
     }
-    if (b < nw + ne) {                               // x = 0, 1, nx-2, nx-1 of rows 2..ny-3
-        const int e = (b - nw) * 128 + ty * 64 + tx;
+    if (b < nwp + nwe) {                             // wall rows at the inlet / outlet columns
+        const int r = b - nwp, side = r % 2, kg = r / 2;
+        const int col = tx % 4, k = kg * 16 + tx / 4;
+        const int i = k < a.nz ? (col < 2 ? col : nx - 4 + col) : nx;   // i = nx: a placeholder
+        const int j = side == 0 ? ty : a.ny - 2 + ty;
+        adjoint_cell<true, SPONGE>(a, i, j, min(k, a.nz - 1), tx, sh);
+        return;
+    }
+    if (b < nwp + nwe + ne) {                        // x = 0, 1, nx-2, nx-1 of rows 2..ny-3
+        const int e = (b - nwp - nwe) * 128 + ty * 64 + tx;
         const int rows = a.ny - 4;
         if (e >= 4 * rows * a.nz) return;
         const int c = e % 4, rr = e / 4;
-        adjoint_cell<false, SPONGE>(a, c < 2 ? c : a.nx - 4 + c, 2 + rr % rows, rr / rows, 0, nullptr);
+        adjoint_cell<false, SPONGE>(a, c < 2 ? c : nx - 4 + c, 2 + rr % rows, rr / rows, 0, nullptr);
         return;
     }
-    const int nb2 = (a.nx / 2 + 63) / 64, rows2 = (a.ny - 4) / BY;
-    const int bi = b - nw - ne;
+    const int nb2 = (nx / 2 + 63) / 64, rows2 = (a.ny - 4) / BY;
+    const int bi = b - nwp - nwe - ne;
     const int bx = bi % nb2, r = bi / nb2;
     const int i0 = 2 * (bx * 64 + tx);
     const int j = 2 + (r % rows2) * BY + ty;
-    if (i0 >= a.nx || (a.inlet && (i0 == 0 || i0 + 2 >= a.nx))) return;
+    if (i0 >= nx || (a.inlet && (i0 == 0 || i0 + 2 >= nx))) return;
     adjoint_pair<SPONGE>(a, i0, j, r / rows2);
 }
 

@@ -913,13 +913,20 @@ void launch_adjoint(lbm_handle *h, const float *sn, const float *lam, float *lou
     sponge_args(h, a.sp_x0, a.sp_inv, a.sp_3nu);
     const bool sponge = a.sp_3nu != 0.0f;
     if (h->nx % 2 == 0) {
-        // one launch: wall rows, the inlet / outlet columns, packed interior pairs
-        const int nw = ((h->nx + 63) / 64) * 2 * h->nz;
-        const int ne = h->opts.inlet && h->ny > 4 ? (4 * (h->ny - 4) * h->nz + 127) / 128 : 0;
+        // one launch: the wall rows (two cells per thread; with the inlet on,
+        // their inlet / outlet columns one cell per thread), the inlet / outlet
+        // columns of the other rows, the packed interior pairs.  With the inlet
+        // on and nx < 6 no wall-row pair is away from both ends: the one-cell
+        // blocks take all four columns.
+        const bool in = h->opts.inlet != 0;
+        const int nwp = (in && h->nx < 6) ? 0 : ((h->nx + 127) / 128) * 2 * h->nz;
+        const int nwe = in ? 2 * ((h->nz + 15) / 16) : 0;
+        const int ne = in && h->ny > 4 ? (4 * (h->ny - 4) * h->nz + 127) / 128 : 0;
         const int ni = h->ny > 4 ? ((h->nx / 2 + 63) / 64) * ((h->ny - 4) / lbmk::BY) * h->nz : 0;
         const dim3 block(64, lbmk::BY);
-        if (sponge) lbmk::adjoint_fused_kernel<true><<<nw + ne + ni, block, 0, h->stream>>>(a, nw, ne);
-        else lbmk::adjoint_fused_kernel<false><<<nw + ne + ni, block, 0, h->stream>>>(a, nw, ne);
+        const unsigned nb = (unsigned)(nwp + nwe + ne + ni);
+        if (sponge) lbmk::adjoint_fused_kernel<true><<<nb, block, 0, h->stream>>>(a, nwp, nwe, ne);
+        else lbmk::adjoint_fused_kernel<false><<<nb, block, 0, h->stream>>>(a, nwp, nwe, ne);
         h->launches += 1;
         return;
     }
@@ -1893,15 +1900,17 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     const bool fused_obj = resolve_kind(h) != LBM_KERNEL_CELL;
     const void *cur = A.ckpt;
     int pp = 0;                                  // next lattice buffer of the ping-pong
-    // the states inside the last segment go straight to the segment slots,
-    // so that the reverse sweep starts without recomputing them
-    const int last_base = T - K;
     // the K - 1 recomputed states of segment s sit in slot set s % 2
     auto slots = [&](int sgm) { return A.seg + (size_t)(sgm % 2) * (K - 1) * L; };
+    // the states inside the last two segments go straight to their slot sets
+    // (one each), so that the reverse sweep recomputes neither of them
+    const int S = T / K;
+    auto stored = [&](int sgm) { return sgm >= S - 2; };
     for (int n = 0; n < T; ++n) {
         void *out;
-        if ((n + 1) % K == 0 && n + 1 < T) out = A.ckpt + (size_t)((n + 1) / K) * L;
-        else if (n + 1 > last_base && n + 1 < T) out = slots(T / K - 1) + (size_t)(n - last_base) * L;
+        const int m = n + 1, sg = m / K;
+        if (m < T && m % K == 0) out = A.ckpt + (size_t)sg * L;
+        else if (m < T && stored(sg)) out = slots(sg) + (size_t)(m % K - 1) * L;
         else { out = h->lat[pp]; pp ^= 1; }
         if (out == cur) { out = h->lat[pp]; pp ^= 1; }
         StepIO io;
@@ -1934,13 +1943,12 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     if ((e = cudaMemsetAsync(A.lamB, 0, L * 4, st)) != cudaSuccess) return cuda_fail(e);
     float *lam = A.lamA, *lout = A.lamB;
     const long long t_end = h->t;
-    const int S = T / K;
     // The recomputation of segment s - 1 is independent of the reverse steps
     // of segment s: with one-launch adjoint steps (nx even) it runs on its own
     // stream beside them, into the other slot set, once the reverse steps of
     // segment s + 1 (which read that set) are done.  Same kernels, same inputs:
     // the results do not depend on the overlap.
-    const bool overlap = h->nx % 2 == 0 && S > 1;
+    const bool overlap = h->nx % 2 == 0 && S > 2;
     if (overlap) {
         if (!h->rstream && (e = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e);
@@ -1974,16 +1982,16 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     };
     for (int sgm = S - 1; sgm >= 0; --sgm) {
         const int base = sgm * K;
-        // this segment's states: from the forward pass (the last one), from the
+        // this segment's states: from the forward pass (the last two), from the
         // recomputation enqueued beside the previous segment, or recomputed here
-        if (sgm != S - 1) {
+        if (!stored(sgm)) {
             if (overlap) {
                 if ((e = cudaStreamWaitEvent(st, h->ev_rec[sgm % 2], 0)) != cudaSuccess) return cuda_fail(e);
             } else if (cudaError_t le = recompute(sgm, st)) {
                 return cuda_fail(le);
             }
         }
-        if (overlap && sgm >= 1) {
+        if (overlap && sgm >= 1 && !stored(sgm - 1)) {
             if (sgm + 1 <= S - 1 &&
                 (e = cudaStreamWaitEvent(h->rstream, h->ev_rev[(sgm + 1) % 2], 0)) != cudaSuccess)
                 return cuda_fail(e);

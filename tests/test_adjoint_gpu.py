@@ -197,6 +197,33 @@ def test_overlapped_recomputation_is_deterministic():
     assert np.allclose(dJa, dJb, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("nx", [48, 47])
+def test_checkpoint_spacing_does_not_change_the_gradient(nx):
+    """The same 24-step window with a checkpoint every 24, 12, 8, 4 and 3
+    steps: one segment (its states all kept by the forward pass), two (both
+    kept), and three or more (the earlier ones recomputed: beside the reverse
+    steps for even nx, in line for odd nx).  The recomputed states are the
+    forward pass's, so the state after the window and dJ/ds_0 are
+    bit-identical, and J and dJ/dtheta agree to the rounding of their FP64
+    atomic sums."""
+    from paper_2304_04214_gb300.channel import LBMChannel
+    ny, nz, N, seed = 16, 8, 16, 27
+    un = stg_uniforms(N, seed)
+    res = []
+    for K in (24, 12, 8, 4, 3):
+        g = LBMChannel(nx, ny, nz, n_modes=N, uniforms=un)
+        g.step(11)
+        J, dJ = g.adjoint_step(24, K, (4, 30, 20))
+        res.append((K, J, dJ, g.adjoint_state_gradient(), g.populations()))
+        g.close()
+    _, J0, dJ0, l0, f0 = res[0]
+    assert np.any(l0 != 0)
+    for K, J, dJ, lam, f in res[1:]:
+        assert abs(J - J0) <= 1e-12 * abs(J0) and np.array_equal(f, f0), (K, J, J0)
+        assert np.array_equal(lam, l0), K
+        assert np.allclose(dJ, dJ0, rtol=1e-12, atol=0), (K, dJ, dJ0)
+
+
 def test_autograd_function_returns_the_adjoint_gradient():
     import torch
     from paper_2304_04214_gb300 import STGAdjoint
