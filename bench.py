@@ -1,7 +1,7 @@
 """Benchmark of the fused D3Q19 MRT-LES + STG channel step on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                [--config c4] [--precision fp32|fp16|bf16]
+                [--config c4] [--precision fp32|fp16|bf16|fp16row]
 
 One bench step is one time step of the method over the whole lattice: the STG
 inlet ring refill (every 64 steps, beside the steps), the interior and wall-row
@@ -44,7 +44,7 @@ CONFIGS = {
     "c4": dict(shape=(1536, 192, 384), re_tau=5200.0, n_modes=400, seed=4,
                name="Re_tau=5200 channel 1536x192x384, N=400 STG modes"),
 }
-BYTES_PER_CELL = {"fp32": 152, "fp16": 76, "bf16": 76}   # 19 loads + 19 stores
+BYTES_PER_CELL = {"fp32": 152, "fp16": 76, "bf16": 76, "fp16row": 76}   # 19 loads + 19 stores
 STATS_EVERY = 10
 
 
@@ -280,14 +280,14 @@ def kernel_pass(ch, steps, stepper=None):
 def storage_sweep(dev, args, barrier, stream, fp32_c4_mlups):
     """Whole-step MLUPS of the other storages and lattices, each the median of
     three timed regions of about 0.3 s: the 16-bit storages at 1536x192x384
-    and FP32 / FP16 at 768x128x192 and 384x96x96, with the FP16 / FP32
-    ratios the 1.6x target refers to."""
+    and FP32 / FP16 / FP16 row base at 768x128x192 and 384x96x96, with the
+    16-bit / FP32 ratios the 1.6x target refers to."""
     import torch
     from paper_2304_04214_gb300.channel import LBMChannel
     peaks, _ = measured_peaks()
     out = {}
-    for key, prec in (("c4", "fp16"), ("c4", "bf16"), ("c3", "fp32"), ("c3", "fp16"),
-                      ("c2", "fp32"), ("c2", "fp16")):
+    for key, prec in (("c4", "fp16"), ("c4", "bf16"), ("c4", "fp16row"), ("c3", "fp32"), ("c3", "fp16"),
+                      ("c3", "fp16row"), ("c2", "fp32"), ("c2", "fp16"), ("c2", "fp16row")):
         if key == args.config and prec == args.precision:
             continue
         cfg = CONFIGS[key]
@@ -312,8 +312,10 @@ def storage_sweep(dev, args, barrier, stream, fp32_c4_mlups):
     m = {k: v["mlups"] for k, v in out.items()}
     if args.config == "c4" and args.precision == "fp32":
         m["c4_fp32"] = fp32_c4_mlups
-    ratios = {c: round(m[f"{c}_fp16"] / m[f"{c}_fp32"], 3) for c in ("c2", "c3", "c4")
-              if f"{c}_fp16" in m and f"{c}_fp32" in m}
+    ratios = {}
+    for prec in ("fp16", "fp16row"):
+        ratios[prec] = {c: round(m[f"{c}_{prec}"] / m[f"{c}_fp32"], 3) for c in ("c2", "c3", "c4")
+                        if f"{c}_{prec}" in m and f"{c}_fp32" in m}
     return out, ratios
 
 
@@ -484,7 +486,8 @@ def run_native(args, cfg, ws, rank, local):
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "storages": sweep,
-            "fp16_over_fp32": ratios,
+            "fp16_over_fp32": ratios["fp16"] if ratios else None,
+            "fp16row_over_fp32": ratios["fp16row"] if ratios else None,
             "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
@@ -535,7 +538,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", default="c4", choices=sorted(CONFIGS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp16row"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "pair", "quad", "staged"])

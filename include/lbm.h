@@ -62,10 +62,16 @@ extern "C" {
 #define LBM_ENOSCRATCH -7   /* larger than the fixed scratch of lbm_wall_shear_noalloc */
 #define LBM_ETIMEOUT   -8   /* a device-side wait gave up (the step's output is invalid) */
 
-/* ---- storage of the populations ---- */
+/* ---- storage of the populations ----
+ * The 16-bit storages keep a deviation, rounded to nearest, and compute in
+ * FP32.  "Row base": the deviation from the equilibrium of the row's mean
+ * flow, f_q - f^eq_q(1, (U0(y_j), 0, 0)), U0 the inlet mean profile (a 19 x ny
+ * table); values about ten times smaller than f_q - w_q in the core flow, so
+ * the rounding noise is that much smaller. */
 #define LBM_FP32      0     /* f_q in FP32 */
-#define LBM_FP16_DEV  1     /* f_q - w_q in IEEE FP16, round to nearest */
-#define LBM_BF16_DEV  2     /* f_q - w_q in BF16, round to nearest */
+#define LBM_FP16_DEV  1     /* f_q - w_q in IEEE FP16 */
+#define LBM_BF16_DEV  2     /* row base in BF16 */
+#define LBM_FP16_ROW  3     /* row base in IEEE FP16 */
 
 typedef struct lbm_handle lbm_handle;
 
@@ -90,7 +96,7 @@ typedef struct {
 } lbm_stg_params;
 
 typedef struct {
-    int precision;            /* LBM_FP32 | LBM_FP16_DEV | LBM_BF16_DEV */
+    int precision;            /* LBM_FP32 | LBM_FP16_DEV | LBM_BF16_DEV | LBM_FP16_ROW */
     double u_bulk;            /* bulk velocity U_b (lattice units), default 0.05 */
     double c_smag;            /* C_smag Delta^2 of eq:smogrinsky_model, default 0.01 */
     double kappa;             /* Reichardt kappa (theta_2), default 0.4 */

@@ -13,9 +13,9 @@ LBM_KERNEL_AUTO, LBM_KERNEL_CELL, LBM_KERNEL_PAIR, LBM_KERNEL_STAGED, LBM_KERNEL
 KERNELS = {"auto": LBM_KERNEL_AUTO, "cell": LBM_KERNEL_CELL, "pair": LBM_KERNEL_PAIR,
            "staged": LBM_KERNEL_STAGED, "quad": LBM_KERNEL_QUAD}
 LBM_NOALLOC_MAX_NX = 32768
-LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2
+LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV, LBM_FP16_ROW = 0, 1, 2, 3
 LBM_FACE_LEFT, LBM_FACE_RIGHT = 0, 1
-PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16_DEV, "bf16": LBM_BF16_DEV}
+PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16_DEV, "bf16": LBM_BF16_DEV, "fp16row": LBM_FP16_ROW}
 
 
 class Grid(ct.Structure):

@@ -114,7 +114,7 @@ STORAGE_CASES = {
 
 
 def storage_report(case, avg_steps=20000, spin_through=2.0, twins=2, stats_every=1):
-    """Long-run profiles of one channel in FP32, FP16 and BF16 storage, and of
+    """Long-run profiles of one channel in FP32, FP16, BF16 and FP16 row-base storage, and of
     FP32 runs started 1e-6 apart (`twins`, the sampling spread of the average):
     spin-up of spin_through domain-through times, then statistics every
     stats_every steps for avg_steps steps; profiles U, <u'u'>, <v'v'>, <w'w'>,
@@ -158,7 +158,7 @@ def storage_report(case, avg_steps=20000, spin_through=2.0, twins=2, stats_every
     out = dict(case=case, lattice=[nx, ny, nz], re_tau=cfg["re_tau"], n_modes=cfg["n_modes"],
                spin_steps=spin, avg_steps=avg_steps, stats_every=stats_every,
                profile_max={k: float(np.max(np.abs(a))) for k, a in zip(names, ref)})
-    for prec in ("fp16", "bf16"):
+    for prec in ("fp16", "bf16", "fp16row"):
         out[prec] = errs(*run(prec))
     out["fp32_twins"] = [errs(*run("fp32", perturb=300 + t)) for t in range(twins)]
     return out
@@ -167,12 +167,12 @@ def storage_report(case, avg_steps=20000, spin_through=2.0, twins=2, stats_every
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--storage-report", choices=sorted(STORAGE_CASES),
-                    help="long-run FP16 / BF16 profile errors against FP32 on a bench lattice")
+                    help="long-run 16-bit profile errors against FP32 on a bench lattice")
     ap.add_argument("--avg-steps", type=int, default=20000)
     ap.add_argument("--re-tau", type=float, default=1000.0)
     ap.add_argument("--lbu", type=int, default=40, help="cells across the channel height H")
     ap.add_argument("--modes", type=int, default=100)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp16row"])
     ap.add_argument("--through", type=float, default=10.0, help="domain-through times in all")
     ap.add_argument("--start", type=float, default=2.0, help="domain-through times before statistics")
     ap.add_argument("--sponge", type=float, default=0.0, help="outlet sponge thickness in delta (0: none)")

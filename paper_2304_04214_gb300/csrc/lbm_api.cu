@@ -800,6 +800,7 @@ cudaError_t launch_step_io(lbm_handle *h, const StepIO &io) {
     switch (h->opts.precision) {
         case LBM_FP16_DEV: return launch_step_t<lbmk::StoreF16>(h, io);
         case LBM_BF16_DEV: return launch_step_t<lbmk::StoreBF16>(h, io);
+        case LBM_FP16_ROW: return launch_step_t<lbmk::StoreF16R>(h, io);
         default: return launch_step_t<lbmk::StoreF32>(h, io);
     }
 }
@@ -1166,7 +1167,7 @@ int lbm_create(const lbm_grid *grid, double re_tau, const lbm_stg_params *stg, c
     if (grid->ny < 4 || grid->ny % 2 || grid->nx < 3 || grid->nz < 1) return LBM_EINVAL;
     if ((long long)grid->nx * grid->ny * grid->nz >= (1ll << 31)) return LBM_EINVAL;
     if (!(re_tau > 0) || stg->n_modes < 0 || (stg->n_modes > 0 && !stg->uniforms)) return LBM_EINVAL;
-    if (opts->precision < LBM_FP32 || opts->precision > LBM_BF16_DEV) return LBM_EINVAL;
+    if (opts->precision < LBM_FP32 || opts->precision > LBM_FP16_ROW) return LBM_EINVAL;
     if (!(opts->u_bulk > 0) || !(opts->kappa > 0) || opts->stats_every < 0) return LBM_EINVAL;
     lbm_handle *h = new (std::nothrow) lbm_handle();
     if (!h) return LBM_ENOMEM;
@@ -1271,6 +1272,7 @@ int lbm_bind_memory(lbm_handle *h, void *dev_ptr, size_t bytes) {
     switch (h->opts.precision) {
         case LBM_FP16_DEV: launch_init<lbmk::StoreF16>(h, h->lat[0]); break;
         case LBM_BF16_DEV: launch_init<lbmk::StoreBF16>(h, h->lat[0]); break;
+        case LBM_FP16_ROW: launch_init<lbmk::StoreF16R>(h, h->lat[0]); break;
         default: launch_init<lbmk::StoreF32>(h, h->lat[0]); break;
     }
     h->cur = 0;
@@ -1485,6 +1487,10 @@ int lbm_get_fields(lbm_handle *h, double *rho, double *u) {
             lbmk::fields_kernel<lbmk::StoreBF16><<<blocks, 256, 0, h->stream>>>(
                 (const __nv_bfloat16 *)h->lat[h->cur], h->d_rowbase, h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
             break;
+        case LBM_FP16_ROW:
+            lbmk::fields_kernel<lbmk::StoreF16R><<<blocks, 256, 0, h->stream>>>(
+                (const __half *)h->lat[h->cur], h->d_rowbase, h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
+            break;
         default:
             lbmk::fields_kernel<lbmk::StoreF32><<<blocks, 256, 0, h->stream>>>(
                 (const float *)h->lat[h->cur], h->d_rowbase, h->d_fw, drho, du, h->nx, h->ny, h->nz, n);
@@ -1516,9 +1522,12 @@ int lbm_get_populations(lbm_handle *h, double *f) {
         if (h->opts.precision == LBM_FP32) f[idx] = ((const float *)buf.data())[idx];
         else if (h->opts.precision == LBM_FP16_DEV)
             f[idx] = kW[q] + (double)__half2float(((const __half *)buf.data())[idx]);
-        else   // f - w as the kernels form it: stored word + row base, in FP32
-            f[idx] = kW[q] + (double)(bf16_to_f32(((const uint16_t *)buf.data())[idx]) +
-                                      h->rb((int)((idx % N) / h->nx % h->ny), q));
+        else {  // row base: f - w as the kernels form it, stored word + row base, in FP32
+            const float word = h->opts.precision == LBM_BF16_DEV
+                                   ? bf16_to_f32(((const uint16_t *)buf.data())[idx])
+                                   : __half2float(((const __half *)buf.data())[idx]);
+            f[idx] = kW[q] + (double)(word + h->rb((int)((idx % N) / h->nx % h->ny), q));
+        }
     }
     return LBM_OK;
 }
@@ -1534,9 +1543,11 @@ int lbm_set_populations(lbm_handle *h, const double *f) {
         if (h->opts.precision == LBM_FP32) ((float *)buf.data())[idx] = (float)f[idx];
         else if (h->opts.precision == LBM_FP16_DEV)
             ((__half *)buf.data())[idx] = __double2half(f[idx] - kW[q]);
-        else
-            ((uint16_t *)buf.data())[idx] =
-                f32_to_bf16_rn((float)(f[idx] - kW[q] - (double)h->rb((int)((idx % N) / h->nx % h->ny), q)));
+        else {
+            const float dev = (float)(f[idx] - kW[q] - (double)h->rb((int)((idx % N) / h->nx % h->ny), q));
+            if (h->opts.precision == LBM_BF16_DEV) ((uint16_t *)buf.data())[idx] = f32_to_bf16_rn(dev);
+            else ((__half *)buf.data())[idx] = __float2half_rn(dev);
+        }
     }
     cudaError_t e;
     if ((e = cudaMemcpyAsync(h->lat[h->cur], buf.data(), n * h->elem, cudaMemcpyHostToDevice, h->stream)) !=

@@ -117,6 +117,11 @@ struct StoreBF16 {
     }
 };
 
+// FP16 words holding the row-base deviation (as StoreBF16 does in BF16).
+struct StoreF16R : StoreF16 {
+    static constexpr bool ROWBASE = true;
+};
+
 // Approximate reciprocal and square root (PTX rcp/sqrt.approx, about one ulp);
 // the collision uses them where a rounding error of that size is harmless.
 __device__ __forceinline__ float rcp_approx(float x) {

@@ -29,9 +29,10 @@ def make_pair(nx, ny, nz, re_tau=1000.0, n_modes=16, seed=1, precision="fp32", i
 
 
 def bf16_row_base(o):
-    """Row base of the BF16 storage, (19, ny) in FP32: f^eq_q(1, (U_R(j), 0, 0))
-    - w_q with the creation-time inlet mean profile U_R of the oracle `o`
-    (the library stores f - w - base and forms f - w in FP32)."""
+    """Row base of the row-base storages (BF16, FP16 row), (19, ny) in FP32:
+    f^eq_q(1, (U_R(j), 0, 0)) - w_q with the creation-time inlet mean profile
+    U_R of the oracle `o` (the library stores f - w - base and forms f - w in
+    FP32)."""
     _, w, _ = cell_api.matrix()
     UR = o.tables()["UR"]
     base = np.stack([cell_api.feq(1.0, (UR[j], 0.0, 0.0)) - w for j in range(len(UR))], axis=1)
@@ -41,7 +42,7 @@ def bf16_row_base(o):
 def quantize_state(f, precision, o=None):
     """Round the stored deviations to the storage type, so that both sides
     start from the same exactly representable state: f - w for FP16, f - w -
-    base(j) for BF16 (needs the oracle `o` for its profile)."""
+    base(j) for BF16 and FP16 row (needs the oracle `o` for its profile)."""
     if precision == "fp32":
         return f.astype(np.float32).astype(np.float64)
     _, w, _ = cell_api.matrix()
@@ -49,7 +50,11 @@ def quantize_state(f, precision, o=None):
     if precision == "fp16":
         return wq + round_to_fp16(f - wq)
     b32 = bf16_row_base(o)[:, None, :, None]
-    r = round_to_bf16(f - wq - b32.astype(np.float64))
+    dev = f - wq - b32.astype(np.float64)
+    if precision == "bf16":
+        r = round_to_bf16(dev)
+    else:   # the library rounds the FP32 value of the deviation
+        r = round_to_fp16(dev.astype(np.float32))
     return wq + (r.astype(np.float32) + b32).astype(np.float64)
 
 

@@ -47,7 +47,7 @@ def oracle_profiles():
     return profiles(s, n)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16", "fp16row"])
 def test_long_run_profiles_match_the_oracle(precision, oracle_profiles):
     _, g = make_pair(NX, NY, NZ, n_modes=100, seed=1, stats=1, precision=precision)
     g.step(STEPS)

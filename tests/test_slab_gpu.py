@@ -29,7 +29,8 @@ def _whole(nx, ny, nz, **kw):
 
 
 @pytest.mark.parametrize("nranks,precision,sponge", [(2, "fp32", None), (3, "fp16", (40, 0.05)),
-                                                      (3, "bf16", None), (2, "fp32", (48, 0.05))])
+                                                      (3, "bf16", None), (2, "fp16row", None),
+                                                      (2, "fp32", (48, 0.05))])
 def test_slabs_are_bit_identical_to_the_undivided_channel(nranks, precision, sponge):
     from paper_2304_04214_gb300.slab import LocalTransport, SlabChannel
     nx, ny, nz, N, seed = 96, 16, 8, 16, 5
