@@ -455,7 +455,7 @@ def run_native(args, cfg, ws, rank, local):
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
-            "repeats": len(regions), "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
+            "repeats": len(regions), "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["name"] + f", {args.precision.upper()} storage",
