@@ -23,7 +23,9 @@ class LBMChannel:
     Fourier modes whose random draws are `uniforms` (n_modes x 4 in [0,1);
     drawn from `seed` by paper_2304_04214_gb300.inputs if not given).
     theta = (ell_e, amp, kappa, B) are the STG length-scale factor and
-    amplitude and the Reichardt constants.
+    amplitude and the Reichardt constants.  precision: "fp32" (f in FP32),
+    "fp16" (f - w in FP16), "bf16" (f - f^eq(1, U0(y)) in BF16) or "fp16row"
+    (f - f^eq(1, U0(y)) in FP16); the arithmetic is FP32 in every case.
     """
 
     def __init__(self, nx, ny, nz, re_tau=1000.0, n_modes=100, uniforms=None, seed=1,
