@@ -417,9 +417,10 @@ typedef struct {
 
 /* Device bytes of the adjoint workspace for a window of `window` steps with a
  * checkpoint every `ckpt_every` steps (window a multiple of ckpt_every):
- * window/ckpt_every checkpoint lattices, two sets of ckpt_every - 1 recomputed
- * lattices (the next segment is recomputed beside the reverse steps of the
- * current one), two adjoint lattices, u_tau of every step, the STG field and
+ * window/ckpt_every checkpoint lattices, three sets of ckpt_every - 1 segment
+ * lattices (the forward pass fills them for the last three segments; the
+ * next segment is recomputed beside the reverse steps of the current one),
+ * two adjoint lattices, u_tau of every step, the STG field and
  * the inlet adjoint of every step.  No device work.  Errors: LBM_EINVAL for
  * window < 1, ckpt_every < 1 or window not a multiple of ckpt_every. */
 int lbm_adjoint_required_bytes(const lbm_handle *h, int window, int ckpt_every, size_t *bytes);
@@ -431,9 +432,9 @@ int lbm_adjoint_bind(lbm_handle *h, int window, int ckpt_every, void *dev_ptr, s
 
 /* Advance the state `window` steps (exactly as lbm_step would), evaluate J over
  * them and its gradient by the hand-written adjoint of the fused step: store
- * s_0 and every ckpt_every-th state (and all states of the last two
- * segments, in the two sets of segment lattices), then for each segment in
- * reverse recompute its states from the checkpoint (except the last two) and
+ * s_0 and every ckpt_every-th state (and all states of the last three
+ * segments, in the three sets of segment lattices), then for each segment in
+ * reverse recompute its states from the checkpoint (except the last three) and
  * run the adjoint steps backwards (for even nx, a segment's recomputation
  * runs on a stream of the handle beside the reverse steps of the segment
  * after it).  *J and dJ_dtheta[4] are host FP64.  dJ/ds_0 is kept for

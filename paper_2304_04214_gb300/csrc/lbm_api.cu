@@ -25,6 +25,10 @@
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+// sets of segment lattices of the adjoint window: the forward pass fills the
+// last kSlotSets segments' sets, the recomputation of the others runs one
+// segment ahead of the reverse steps
+constexpr int kSlotSets = 3;
 
 // Carves one device allocation into 256-byte aligned buffers.  With guard
 // bands on (guard > 0, a debugging aid), a band of at least `guard` bytes sits
@@ -183,7 +187,7 @@ struct lbm_handle {
     // lbm_adjoint_step: the recomputation of the next segment beside the
     // reverse steps of the current one (its own stream; events per slot set)
     cudaStream_t rstream = nullptr;
-    cudaEvent_t ev_rstart = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
+    cudaEvent_t ev_rstart = nullptr, ev_rec[kSlotSets] = {}, ev_rev[kSlotSets] = {};
     cudaEvent_t ev_aux_fork = nullptr, ev_aux_join = nullptr;
     // inlet profile uploads (lbm_set_inlet_profile): pinned staging of U_R and
     // amp chol(R), one half per device buffer, copied on their own stream;
@@ -445,7 +449,7 @@ struct lbm_handle {
         const size_t L = 19 * (size_t)ncell, W = 2 * (size_t)nz * nx, I = 3 * (size_t)nz * ny;
         const size_t N = n_modes > 0 ? n_modes : 1;
         adj.ckpt = ar.take<float>(L * (T / K));
-        adj.seg = ar.take<float>(L * 2 * (K - 1));     // two sets of K - 1 segment slots
+        adj.seg = ar.take<float>(L * kSlotSets * (K - 1));   // kSlotSets sets of K - 1 segment slots
         adj.lamA = ar.take<float>(L);
         adj.lamB = ar.take<float>(L);
         adj.ut_init = ar.take<float>(W);
@@ -1911,12 +1915,12 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     const bool fused_obj = resolve_kind(h) != LBM_KERNEL_CELL;
     const void *cur = A.ckpt;
     int pp = 0;                                  // next lattice buffer of the ping-pong
-    // the K - 1 recomputed states of segment s sit in slot set s % 2
-    auto slots = [&](int sgm) { return A.seg + (size_t)(sgm % 2) * (K - 1) * L; };
-    // the states inside the last two segments go straight to their slot sets
-    // (one each), so that the reverse sweep recomputes neither of them
+    // the K - 1 recomputed states of segment s sit in slot set s % kSlotSets
+    auto slots = [&](int sgm) { return A.seg + (size_t)(sgm % kSlotSets) * (K - 1) * L; };
+    // the states inside the last kSlotSets segments go straight to their slot
+    // sets (one each), so that the reverse sweep recomputes none of them
     const int S = T / K;
-    auto stored = [&](int sgm) { return sgm >= S - 2; };
+    auto stored = [&](int sgm) { return sgm >= S - kSlotSets; };
     for (int n = 0; n < T; ++n) {
         void *out;
         const int m = n + 1, sg = m / K;
@@ -1956,16 +1960,19 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     const long long t_end = h->t;
     // The recomputation of segment s - 1 is independent of the reverse steps
     // of segment s: with one-launch adjoint steps (nx even) it runs on its own
-    // stream beside them, into the other slot set, once the reverse steps of
-    // segment s + 1 (which read that set) are done.  Same kernels, same inputs:
-    // the results do not depend on the overlap.
-    const bool overlap = h->nx % 2 == 0 && S > 2;
+    // stream beside them, into its slot set, once the reverse steps of
+    // segment s - 1 + kSlotSets (which read that set) are done.  Same kernels,
+    // same inputs: the results do not depend on the overlap.
+    const bool overlap = h->nx % 2 == 0 && S > kSlotSets;
     if (overlap) {
         if (!h->rstream && (e = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e);
-        for (cudaEvent_t *ev : {&h->ev_rstart, &h->ev_rec[0], &h->ev_rec[1], &h->ev_rev[0], &h->ev_rev[1]})
-            if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
-                return cuda_fail(e);
+        if (!h->ev_rstart && (e = cudaEventCreateWithFlags(&h->ev_rstart, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e);
+        for (int c = 0; c < kSlotSets; ++c)
+            for (cudaEvent_t *ev : {&h->ev_rec[c], &h->ev_rev[c]})
+                if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+                    return cuda_fail(e);
         // the checkpoints, u_tau history and STG field of the forward pass are ready
         if ((e = cudaEventRecord(h->ev_rstart, st)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(h->rstream, h->ev_rstart, 0)) != cudaSuccess)
@@ -1993,21 +2000,24 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
     };
     for (int sgm = S - 1; sgm >= 0; --sgm) {
         const int base = sgm * K;
-        // this segment's states: from the forward pass (the last two), from the
-        // recomputation enqueued beside the previous segment, or recomputed here
+        // this segment's states: from the forward pass (the last kSlotSets),
+        // from the recomputation enqueued beside the previous segment, or
+        // recomputed here
         if (!stored(sgm)) {
             if (overlap) {
-                if ((e = cudaStreamWaitEvent(st, h->ev_rec[sgm % 2], 0)) != cudaSuccess) return cuda_fail(e);
+                if ((e = cudaStreamWaitEvent(st, h->ev_rec[sgm % kSlotSets], 0)) != cudaSuccess) return cuda_fail(e);
             } else if (cudaError_t le = recompute(sgm, st)) {
                 return cuda_fail(le);
             }
         }
         if (overlap && sgm >= 1 && !stored(sgm - 1)) {
-            if (sgm + 1 <= S - 1 &&
-                (e = cudaStreamWaitEvent(h->rstream, h->ev_rev[(sgm + 1) % 2], 0)) != cudaSuccess)
+            const int last_reader = sgm - 1 + kSlotSets;      // the previous user of that set
+            if (last_reader <= S - 1 &&
+                (e = cudaStreamWaitEvent(h->rstream, h->ev_rev[last_reader % kSlotSets], 0)) != cudaSuccess)
                 return cuda_fail(e);
             if (cudaError_t le = recompute(sgm - 1, h->rstream)) return cuda_fail(le);
-            if ((e = cudaEventRecord(h->ev_rec[(sgm - 1) % 2], h->rstream)) != cudaSuccess) return cuda_fail(e);
+            if ((e = cudaEventRecord(h->ev_rec[(sgm - 1) % kSlotSets], h->rstream)) != cudaSuccess)
+                return cuda_fail(e);
         }
         for (int n = base + K - 1; n >= base; --n) {
             const float *sn = n == base ? A.ckpt + (size_t)sgm * L : slots(sgm) + (size_t)(n - base - 1) * L;
@@ -2015,7 +2025,7 @@ int lbm_adjoint_step(lbm_handle *h, int window, int ckpt_every, const lbm_object
                            h->opts.inlet ? A.luin + (size_t)n * I : nullptr, true, obj, jtau_w);
             std::swap(lam, lout);
         }
-        if (overlap && (e = cudaEventRecord(h->ev_rev[sgm % 2], st)) != cudaSuccess) return cuda_fail(e);
+        if (overlap && (e = cudaEventRecord(h->ev_rev[sgm % kSlotSets], st)) != cudaSuccess) return cuda_fail(e);
         // theta gradient through this segment's inlet velocities, beside the
         // next segment's reverse steps
         if (h->opts.inlet) {
@@ -2323,8 +2333,10 @@ void lbm_destroy(lbm_handle *h) {
     if (h->ev_shear) cudaEventDestroy(h->ev_shear);
     graphs_clear(h);
     if (h->rstream) { cudaStreamSynchronize(h->rstream); cudaStreamDestroy(h->rstream); }
-    for (cudaEvent_t ev : {h->ev_rstart, h->ev_rec[0], h->ev_rec[1], h->ev_rev[0], h->ev_rev[1]})
-        if (ev) cudaEventDestroy(ev);
+    if (h->ev_rstart) cudaEventDestroy(h->ev_rstart);
+    for (int c = 0; c < kSlotSets; ++c)
+        for (cudaEvent_t ev : {h->ev_rec[c], h->ev_rev[c]})
+            if (ev) cudaEventDestroy(ev);
     if (h->ev_gfork) cudaEventDestroy(h->ev_gfork);
     if (h->ev_gjoin) cudaEventDestroy(h->ev_gjoin);
     if (h->gstream) cudaStreamDestroy(h->gstream);

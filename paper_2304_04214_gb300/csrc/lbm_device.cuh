@@ -346,8 +346,12 @@ __device__ __forceinline__ void collide_mrt(float (&f)[19], const Pairs &P, floa
 typedef float2 V2;
 __device__ __forceinline__ V2 vdup(float s) { return make_float2(s, s); }
 __device__ __forceinline__ V2 operator+(V2 a, V2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return __ffma2_rn(b, vdup(-1.0f), a); }
-__device__ __forceinline__ V2 operator-(V2 a) { return __fmul2_rn(a, vdup(-1.0f)); }
+// a - b as a packed add of the negated operand: the negation folds into the
+// add, where a multiply-add with a (-1, -1) pair needs that pair in registers
+// (measured: 1-2% off the 16-bit step kernels, which are bound by instruction
+// issue)
+__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ V2 operator-(V2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ V2 operator*(V2 a, V2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ V2 operator*(float s, V2 b) { return __fmul2_rn(vdup(s), b); }
 __device__ __forceinline__ V2 operator*(V2 b, float s) { return __fmul2_rn(b, vdup(s)); }

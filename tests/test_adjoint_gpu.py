@@ -199,10 +199,10 @@ def test_overlapped_recomputation_is_deterministic():
 
 @pytest.mark.parametrize("nx", [48, 47])
 def test_checkpoint_spacing_does_not_change_the_gradient(nx):
-    """The same 24-step window with a checkpoint every 24, 12, 8, 4 and 3
-    steps: one segment (its states all kept by the forward pass), two (both
-    kept), and three or more (the earlier ones recomputed: beside the reverse
-    steps for even nx, in line for odd nx).  The recomputed states are the
+    """The same 24-step window with a checkpoint every 24, 12, 8, 6, 4 and 3
+    steps: up to three segments (their states all kept by the forward pass),
+    and four or more (the earlier ones recomputed: beside the reverse steps
+    for even nx, in line for odd nx).  The recomputed states are the
     forward pass's, so the state after the window and dJ/ds_0 are
     bit-identical, and J and dJ/dtheta agree to the rounding of their FP64
     atomic sums."""
@@ -210,7 +210,7 @@ def test_checkpoint_spacing_does_not_change_the_gradient(nx):
     ny, nz, N, seed = 16, 8, 16, 27
     un = stg_uniforms(N, seed)
     res = []
-    for K in (24, 12, 8, 4, 3):
+    for K in (24, 12, 8, 6, 4, 3):
         g = LBMChannel(nx, ny, nz, n_modes=N, uniforms=un)
         g.step(11)
         J, dJ = g.adjoint_step(24, K, (4, 30, 20))
