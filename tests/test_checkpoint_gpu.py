@@ -34,7 +34,7 @@ def _custom_profile(ch):
     ch.lib.lbm_set_inlet_profile(ch.h, dp(U), dp(R))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16", "fp16row"])
 def test_resume_is_bit_identical(tmp_path, precision):
     a = _channel(precision)
     _custom_profile(a)

@@ -40,7 +40,7 @@ def _same(a, b):
     assert np.array_equal(sa, sb) and np.array_equal(ua, ub)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "fp16row"])
 def test_graph_periods_are_bit_identical_to_separate_launches(precision):
     a, b = _pair(precision)
     for n in (300, 1, 399, 64, 128):

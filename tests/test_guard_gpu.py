@@ -33,6 +33,7 @@ def _dp(a):
     ((129, 12, 5), "fp32", "cell"),     # odd nx: the one-cell kernel, objective kernel
     ((136, 12, 5), "fp16", "staged"),   # ragged last TMA tile
     ((64, 8, 3), "bf16", "quad"),
+    ((68, 10, 4), "fp16row", "quad"),   # nx not a multiple of 128: a ragged warp
     ((48, 4, 1), "fp32", "auto"),       # wall rows only, one z plane
 ])
 def test_guard_bands_stay_intact(shape, precision, kernel):
