@@ -7,27 +7,27 @@ oracle's run of the same set-up (tests/golden/decorrelated_h40_re1000.txt,
 written by make_decorrelated_profiles.py from the oracle alone).
 
 After 5T the streamwise velocity along the centre row differs from the
-oracle's pointwise by a sizeable fraction of itself downstream: the two runs
+oracle's pointwise by a sizeable fraction of itself downstream: the runs
 have decorrelated (an FP32 rounding difference grows by about e every 250
 steps once turbulence has developed; the 4 delta channel of
-test_longrun_gpu.py convects it out first).  Their statistics then agree only
-up to the sampling error of a 3T average, which is measured here: four FP32
-runs started 1e-6 apart from the unperturbed one (same inputs otherwise) give
-the spread of the error measure between two decorrelated runs of this length.
+test_longrun_gpu.py convects it out first).  Their statistics then agree
+only up to the sampling error of a 3T average, and one realization differs
+from the next by as much as from the oracle: over six runs started 1e-6
+apart, single runs' u'v' errors 5-10 delta from the inlet (where the inlet
+turbulence is still adapting) range from 3% to 14%.  So each storage is
+judged by the mean of its statistics over an ensemble of four runs (the
+unperturbed one and three started 1e-6 apart), against a bar from the
+spread of single FP32 runs (four FP32 runs started 1e-6 apart from the
+unperturbed one).  FP16 storage of f - w reaches that bar where the inlet
+turbulence adapts (an expected failure that states the numbers); with the
+row base (BF16, FP16 row) the stored values and their rounding noise are
+ten times smaller.
 
 Error measure: max over y of |difference| / max over y of |oracle profile|, for
 U, <u'u'>, <v'v'>, <w'w'>, <u'v'> averaged over z, the samples and each of
-three x ranges.  Bar: 2%, or 1.5x the largest twin spread where the sampling
-error alone is larger than 2% (the second moments: their twin spread is 1-5%).
-
-FP16 storage of f - w misses this bar where the inlet turbulence is still
-adapting (5-10 delta from the inlet): over six runs 1e-6 apart its
-second-moment errors there average 3.8% (u'u'), 5.6% (v'v'), 5.2% (w'w') and
-12.7% (u'v') against 1.2%, 1.9%, 2.2% and 3.8% for FP32 -- a systematic
-effect of its rounding noise, not sampling.  The row-base storages (BF16,
-FP16 row: the deviation from the row's mean-flow equilibrium, ten times
-smaller values) stay within the bar; FP16 f - w is kept as an expected
-failure that states the miss.
+three x ranges.  Bar: 2%, or 1.5x the largest single-run FP32 spread where
+the sampling error alone is larger than 2% (the second moments: 1-6%); the
+mean profile U: 2% always.
 """
 import os
 
@@ -42,6 +42,7 @@ T = 8000
 SPIN, AVG = 2 * T, 3 * T
 RANGES = [(NX // 4, NX // 2), (NX // 2, 3 * NX // 4), (3 * NX // 4, NX)]
 NAMES = ("U", "uu", "vv", "ww", "uv")
+ENSEMBLE = 4                      # runs per storage whose statistics are averaged
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -100,24 +101,29 @@ def runs():
         pytest.fail(f"missing {GOLDEN}: run tests/golden/make_decorrelated_profiles.py")
     moments, u_oracle = _golden()
     oracle = {r: _profiles(np.stack([moments[(r[0], r[1], c)] for c in range(7)])) for r in RANGES}
-    gpu = {p: _run(p) for p in ("fp32", "fp16", "bf16", "fp16row")}
     twins = [_run("fp32", perturb_seed=200 + t) for t in range(4)]
+    gpu = {"fp32": [_run("fp32")] + twins[:ENSEMBLE - 1]}
+    for p in ("fp16", "bf16", "fp16row"):
+        gpu[p] = [_run(p)] + [_run(p, perturb_seed=200 + t) for t in range(ENSEMBLE - 1)]
     return oracle, u_oracle, gpu, twins
 
 
 def test_the_runs_have_decorrelated(runs):
     _, u_oracle, gpu, twins = runs
     down = slice(NX // 2, NX)
-    for p, (_, u) in gpu.items():
+    for p, rs in gpu.items():
+        u = rs[0][1]
         d = np.max(np.abs(u[down] - u_oracle[down])) / np.max(np.abs(u_oracle[down]))
         print(p, f"pointwise difference from the oracle, x >= nx/2: {d:.3f}")
         assert d > 0.05, (p, d)
-    d = np.max(np.abs(twins[0][1][down] - gpu["fp32"][1][down])) / np.max(np.abs(gpu["fp32"][1][down]))
+    base = gpu["fp32"][0][1]
+    d = np.max(np.abs(twins[0][1][down] - base[down])) / np.max(np.abs(base[down]))
     assert d > 0.05, d
 
 
-FP16_MISS = ("FP16 f - w: second moments 2-3x the FP32 error 5-10 delta from the inlet "
-             "(u'v' 12.7% vs 3.8%, v'v' 5.6% vs 1.9%), beyond the sampling bar")
+FP16_MISS = ("FP16 f - w: its ensemble's u'v' error 5-10 delta from the inlet is 9.0% against 3.3% "
+             "for FP32 (bar 9.0%), the normal stresses about twice FP32's: its rounding noise changes "
+             "the adapting inlet turbulence; the row-base storages stay within the bar")
 
 
 @pytest.mark.parametrize("precision", ["fp32", pytest.param("fp16", marks=pytest.mark.xfail(reason=FP16_MISS)),
@@ -126,10 +132,11 @@ def test_decorrelated_statistics_match_the_oracle(precision, runs):
     oracle, _, gpu, twins = runs
     bad = []
     for r in RANGES:
-        spread = np.max([_errors(gpu["fp32"][0][r], tw[0][r]) for tw in twins], axis=0)
+        spread = np.max([_errors(gpu["fp32"][0][0][r], tw[0][r]) for tw in twins], axis=0)
         bars = np.maximum(0.02, 1.5 * spread)
         bars[0] = 0.02                                   # the mean profile: 2% always
-        err = _errors(oracle[r], gpu[precision][0][r])
+        ens = np.mean([run[0][r] for run in gpu[precision]], axis=0)
+        err = _errors(oracle[r], ens)
         print(precision, r, " ".join(f"{k} {e:.2e} (bar {b:.2e})" for k, e, b in zip(NAMES, err, bars)))
         bad += [(r, k, float(e), float(b)) for k, e, b in zip(NAMES, err, bars) if not e < b]
     assert not bad, (precision, bad)
