@@ -217,7 +217,7 @@ def run_reference(args, cfg, ws, rank):
     line = {
         "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(1e3 * dt / n, 3), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": round(1e3 * dt / n, 3), "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": cfg["name"] + " (oracle on a spanwise slice)", "storage": "fp64",
                    "lattice": list(cfg["shape"]), "sample_lattice": [nx, ny, nzs]},
